@@ -1,0 +1,215 @@
+/*
+ * saq.h -- C ABI of the GB300-native SAQ vector encoder.
+ *
+ * SAQ (Segmented CAQ, arXiv 2509.12086) maps each data vector o_r to a
+ * compact code from which distances to query vectors can be estimated
+ * (Sec. 1 problem statement; Sec. 2.2 Eq. 2-3).  The library implements the
+ * fit (Sec. 4.1 PCA, Sec. 4.2 Algorithm 2, per-segment random rotations), the
+ * encode hot path (Sec. 3.1 Eq. rotate, Eq. find_nearest_code, Algorithm 1,
+ * Sec. 4.2 per-segment quantization, Sec. 5.1 combined PCA+rotation matrix)
+ * and the distance estimator (Sec. 3.2 Eq. estimator_inner_product).
+ *
+ * Conventions for every entry point:
+ *   - Plain pointers and sizes only.  "_dev" pointers are CUDA device
+ *     pointers on the current device; "_host" pointers are host memory.
+ *   - Device buffers passed in must be 16-byte aligned.
+ *   - The caller owns every data buffer it passes; the library owns models.
+ *   - Calls that take a `stream` (a cudaStream_t passed as void*, NULL for
+ *     the legacy default stream) are asynchronous on that stream unless
+ *     stated otherwise; buffers must stay valid until the stream reaches the
+ *     call's work.
+ *   - Errors are returned as saq_status; no exception crosses the ABI.
+ *     Arguments are validated before any launch.  saq_last_error() returns a
+ *     message for the calling thread's last failure.
+ *   - A model may be used by one encode/estimate call at a time per stream;
+ *     concurrent calls on different streams with the same model are allowed
+ *     (the model is read-only during encode; scratch is stream-ordered).
+ */
+#ifndef SAQ_H
+#define SAQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct saq_model saq_model;
+
+typedef enum {
+    SAQ_OK = 0,
+    SAQ_ERR_INVALID = 1,     /* bad argument; nothing was launched          */
+    SAQ_ERR_CUDA = 2,        /* a CUDA runtime / library call failed        */
+    SAQ_ERR_OOM = 3,         /* device or host allocation failed            */
+    SAQ_ERR_TIMEOUT = 4,     /* a bounded device wait gave up               */
+    SAQ_ERR_UNSUPPORTED = 5  /* valid request the build does not support    */
+} saq_status;
+
+/* Arithmetic of the projection GEMM (Sec. 5.1 combined matrix).  Quantization
+ * and code adjustment always run in FP32.
+ *   SAQ_PREC_FP32: FP32 inputs; tensor-core GEMM with a three-term FP16
+ *                  split of both operands and FP32 accumulation (error on
+ *                  the order of FP32 rounding).
+ *   SAQ_PREC_FP32_SIMT: FP32 CUDA-core GEMM (reference-grade, slow).
+ *   SAQ_PREC_BF16: BF16 operands on the tensor cores, FP32 accumulation.
+ *   SAQ_PREC_FP8:  FP8 e4m3 operands with per-segment scales, FP32
+ *                  accumulation. */
+typedef enum {
+    SAQ_PREC_FP32 = 0,
+    SAQ_PREC_BF16 = 1,
+    SAQ_PREC_FP8 = 2,
+    SAQ_PREC_FP32_SIMT = 3
+} saq_precision;
+
+/* Fit parameters (Sec. 4.1-4.2; Sec. 3.1 for rounds). */
+typedef struct {
+    double avg_bits;          /* bit quota Q_quota = round(avg_bits * d)      */
+    int32_t max_bits;         /* valid per-segment bits are 0..max_bits (<=8) */
+    int32_t rounds;           /* code-adjustment rounds r of Algorithm 1      */
+    int32_t seg_granularity;  /* segment length multiple g (paper: 64)        */
+    int32_t precision;        /* saq_precision of the projection GEMM         */
+    double tie_frac;          /* plan: fewest segments within (1+tie_frac) of
+                                 the least modelled error (paper: 0.1%)      */
+    uint64_t seed;            /* seed of the per-segment random rotations     */
+} saq_params;
+
+/* One segment of a quantization plan (Sec. 4.1 tuple (Seg, B)): PCA
+ * dimensions [start, start+len) quantized with `bits` bits each; bits == 0
+ * drops the segment. */
+typedef struct {
+    int32_t start;
+    int32_t len;
+    int32_t bits;
+} saq_segment;
+
+/* Fill *p with the defaults: avg_bits 4, max_bits 8, rounds 6, granularity
+ * 64, precision FP32, tie_frac 1e-3, seed 4. */
+void saq_params_init(saq_params *p);
+
+/*
+ * Fit a model on n rows of X_dev (device, row-major n x d FP32):
+ * mean c and FP64 covariance on the GPU, eigen-decomposition (sigma^2
+ * descending, Sec. 4.1), plan by Algorithm 2 with
+ * ERROR(Seg,B) = sum sigma_i^2 2^-B (Eq. seg-err, empirical-variance form),
+ * a seeded random orthonormal matrix per kept segment, and the combined
+ * matrix W = blockdiag(R_s) V_kept^T (Sec. 5.1).  Synchronous: returns after
+ * the model is ready.  n >= 2, d >= 1.  *out receives a new model owned by
+ * the caller (free with saq_model_free).
+ */
+saq_status saq_fit(const float *X_dev, int64_t n, int32_t d,
+                   const saq_params *p, saq_model **out, void *stream);
+
+/*
+ * Build a model from explicit host arrays (FP64): mean[d]; plan[nseg]
+ * covering [0, d) in order; W[d_kept x d] row-major, the rows of the kept
+ * segments in plan order (d_kept = sum of len over segments with bits > 0);
+ * sig2[d] optional (may be NULL).  Only p->rounds and p->precision are used.
+ * Copies everything; synchronous.
+ */
+saq_status saq_model_create(int32_t d, const double *mean, const double *W,
+                            const saq_segment *plan, int32_t nseg,
+                            const double *sig2, const saq_params *p,
+                            saq_model **out);
+
+void saq_model_free(saq_model *m);
+
+/* Model queries.  Code layout: per vector, code_bytes bytes; per kept
+ * segment in plan order, `bits` bit-planes, most significant first; plane p
+ * holds bit (bits-1-p) of every code of the segment as ceil(len/64)
+ * little-endian 64-bit words (coordinate i -> word i/64, bit i%64).  The
+ * first b planes of a segment are its b-bit prefix code (Sec. 3.2).
+ * Factor layout: per vector factor_count FP32 values:
+ * [ |o_r - c|^2, then per kept segment |o_s|, cos_s ], where cos_s is the
+ * cosine between the adjusted quantized vector and o_s (Sec. 3.1 end). */
+size_t saq_code_bytes(const saq_model *m);
+int32_t saq_factor_count(const saq_model *m);
+int32_t saq_model_dim(const saq_model *m);
+int32_t saq_model_kept_dim(const saq_model *m);
+int32_t saq_model_num_segments(const saq_model *m);   /* all, incl. dropped */
+saq_status saq_model_get_plan(const saq_model *m, saq_segment *out, int32_t cap);
+saq_status saq_model_get_mean(const saq_model *m, double *out /* d */);
+saq_status saq_model_get_matrix(const saq_model *m, double *out /* d_kept x d */);
+saq_status saq_model_get_variances(const saq_model *m, double *out /* d */);
+/* Change the GEMM precision (saq_precision) or the number of adjustment
+ * rounds of an existing model.  Synchronous; not concurrent with encodes. */
+saq_status saq_model_set_precision(saq_model *m, int32_t precision);
+saq_status saq_model_set_rounds(saq_model *m, int32_t rounds);
+
+/*
+ * Encode n vectors (the hot path).  X_dev: device, row-major n x d FP32.
+ * Per vector: o = W (x - c) (Sec. 3.1 Eq. rotate with the combined PCA +
+ * segment-rotation matrix of Sec. 5.1); per kept segment: v_max, Delta and
+ * the initial code of Eq. find_nearest_code (o = v_max clamps to 2^B - 1),
+ * then r rounds of Algorithm 1 (+Delta tried before -Delta, a move kept only
+ * if it stays in range and strictly raises cos(x, o); a round without a move
+ * ends the segment early, which changes no result); then the factors and the
+ * bit-plane codes.  Outputs: codes_dev n x code_bytes, factors_dev
+ * n x factor_count FP32.  Asynchronous on `stream`.  n == 0 is a no-op.
+ * Scratch memory comes from the stream-ordered allocator (cudaMallocAsync)
+ * and is returned before the call's work completes on the stream.
+ */
+saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n,
+                      uint8_t *codes_dev, float *factors_dev, void *stream);
+
+/*
+ * Same as saq_encode, with host buffers: the rows are copied to the device
+ * in chunks, encoded and the codes and factors copied back, with copies of
+ * one chunk overlapping the encode of the next.  Page-locked host memory is
+ * strongly recommended.  Synchronous: returns when the outputs are in host
+ * memory.
+ */
+saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
+                           uint8_t *codes_host, float *factors_host,
+                           void *stream);
+
+/*
+ * The two halves of saq_encode, for testing and for callers that already
+ * hold projected vectors.
+ * saq_project: O_dev (n x d_kept FP32, row-major) = W (x - c) with the
+ *   model's precision, norms2_dev[n] = |x - c|^2.
+ * saq_quantize_projected: quantize and adjust O_dev as saq_encode does and
+ *   write codes and factors; factor 0 of each vector is taken from
+ *   norms2_dev.
+ */
+saq_status saq_project(const saq_model *m, const float *X_dev, int64_t n,
+                       float *O_dev, float *norms2_dev, void *stream);
+saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
+                                  const float *norms2_dev, int64_t n,
+                                  uint8_t *codes_dev, float *factors_dev,
+                                  void *stream);
+
+/*
+ * Estimated squared distances dist_dev[q * n + v] between query q (rows of
+ * Q_dev, device nq x d FP32) and encoded vector v:
+ *   |o_r - q_r|^2 ~ |o_r - c|^2 + |q_r - c|^2 - 2 sum_s est_s      (Eq. 3)
+ *   est_s = |o_s| <u_s, q_s> / (|u_s| cos_s),  u_s = 2 c_a - (2^B - 1)
+ * which is the estimator <o_bar_a, q>/<o_bar_a, o> |o|^2 of Sec. 3.2 per
+ * segment, with q_s the query rotated by the same matrix.  prefix_bits > 0
+ * uses the b = min(prefix_bits, B) most significant bits of every code
+ * (progressive approximation, Sec. 3.2) with the stored factors; 0 uses all
+ * bits.  Asynchronous on `stream`.
+ */
+saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
+                             const float *factors_dev, int64_t n,
+                             const float *Q_dev, int64_t nq,
+                             int32_t prefix_bits, float *dist_dev,
+                             void *stream);
+
+/*
+ * Serialise a model (mean, plan, W, sigma^2, rounds, precision) into a
+ * versioned little-endian blob.  With buf == NULL, *len receives the size.
+ * Otherwise *len is the capacity of buf and receives the bytes written.
+ */
+saq_status saq_model_export(const saq_model *m, void *buf, size_t *len);
+saq_status saq_model_import(const void *buf, size_t len, saq_model **out);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *saq_last_error(void);
+const char *saq_status_string(saq_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAQ_H */
