@@ -1,0 +1,341 @@
+"""SAQ encode benchmark: encoded vectors/s on one GB300 (or N replicas).
+
+A step is one full pass of the encode hot path (projection GEMM, per-segment
+initial quantization, code adjustment, factors and bit-packing) over the whole
+batch of the workload, inputs resident in HBM.  Default workload: 1,000,000
+vectors of d = 960 drawn with a power-law spectrum (alpha = 0.8) under a
+seeded random rotation, 4 bits/dim on average, 6 adjustment rounds, FP32
+projection.  The batch (3.84 GB) is larger than L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import paper_2509_12086_gb300 as P  # noqa: E402
+from paper_2509_12086_gb300 import synth  # noqa: E402
+
+METRIC = "SAQ encoded vectors/s at d=960 4b/dim, FP32 vs BF16; ingest p50/p99 latency"
+UNIT = "vectors/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            j = json.load(f)
+        return {"hbm_gbs": j["hbm_gbs"], "bf16_tflops": j["bf16_tflops"],
+                "bf16_tflops_sustained": j.get("bf16_tflops_sustained", j["bf16_tflops"]),
+                "sm_max_mhz": j.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world <= 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_desc(w, name, precision, plan, code_bytes):
+    return {"workload": "%s: N=%d d=%d power-law alpha=%.1f under a seeded random rotation, "
+                        "%.0f b/dim avg, r=%d, %s projection" % (
+                            name, w["n"], w["d"], w["alpha"], w["avg_bits"], w["rounds"],
+                            precision),
+            "n": w["n"], "d": w["d"], "alpha": w["alpha"], "avg_bits": w["avg_bits"],
+            "rounds": w["rounds"], "precision": precision, "plan": plan,
+            "code_bytes": code_bytes,
+            "l2": "inputs (%.2f GB) larger than L2 (129 MB): no flush" % (w["n"] * w["d"] * 4 / 1e9)}
+
+
+def cpu_baseline(w, X_dev, target_s=12.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the same workload (fit on its own subsample, not timed)."""
+    import oracle as O
+    fit_rows = min(w["n"], 50000)
+    Xf = X_dev[:fit_rows].cpu().numpy()
+    mo = O.fit(Xf, w["avg_bits"])
+    probe = Xf[:2000]
+    t0 = time.perf_counter()
+    O.encode(probe, mo, rounds=w["rounds"])
+    per = (time.perf_counter() - t0) / probe.shape[0]
+    ns = int(min(fit_rows, max(2000, target_s / max(per, 1e-9))))
+    Xs = Xf[:ns]
+    t0 = time.perf_counter()
+    O.encode(Xs, mo, rounds=w["rounds"])
+    dt = time.perf_counter() - t0
+    return {"value": ns / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": "%d rows of the workload (oracle fit on %d rows, not timed): "
+                      "FP64 projection + CAQ + factors, %.1f s" % (ns, fit_rows, dt)}, mo
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    w = dict(synth.WORKLOADS[args.workload])
+    X = synth.power_law(min(w["n"], 60000), w["d"], w["alpha"]).numpy()
+    mo = O.fit(X[:50000], w["avg_bits"])
+    sample = X[50000:50000 + args.ref_rows] if X.shape[0] > 50000 else X[:args.ref_rows]
+    for _ in range(args.warmup):
+        O.encode(sample[:500], mo, rounds=w["rounds"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.encode(sample, mo, rounds=w["rounds"])
+    dt = time.perf_counter() - t0
+    value = sample.shape[0] * args.steps / dt
+    cfg = workload_desc(w, args.workload, "fp64 (oracle)", mo.plan, mo.code_bytes)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.max_threads(),
+                            "kind": "oracle",
+                            "sample": "%d rows per step, oracle fit on 50000 rows" % sample.shape[0]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def time_events(fn, iters, stream):
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(iters):
+        fn()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(stop) / 1e3 / iters
+
+
+def run_ours(args):
+    world, rank, local = dist_setup()
+    pk = peaks()
+    w = dict(synth.WORKLOADS[args.workload])
+    if args.n:
+        w["n"] = args.n
+    n, d = w["n"], w["d"]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    # each rank encodes its own batch (weak scaling, no collective on the data path)
+    X = synth.power_law(n, d, w["alpha"], seed=synth.SEED_DATA + 7919 * rank, device=dev)
+    m = P.saq_fit(X, avg_bits=w["avg_bits"], rounds=w["rounds"], precision=args.precision)
+    codes, factors = m.alloc_outputs(n, dev)
+
+    def step():
+        m.encode(X, codes, factors)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = P.saq_kernel_launch_count()
+    t_dev = time_events(step, args.steps, stream) * args.steps
+    launches = P.saq_kernel_launch_count() - l0
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_max = max_over_ranks(world, t_dev)
+    value = n * world * args.steps / t_max
+
+    # per-kernel breakdown of one step: projection alone and quantization alone
+    O_buf, nrm = m.project(X[:min(n, 262144)])
+    rows = O_buf.shape[0]
+    t_proj = time_events(lambda: m.project(X[:rows]), 3, stream) * n / rows
+    Oc = O_buf.contiguous()
+    t_caq = time_events(lambda: m.quantize_projected(Oc, nrm), 3, stream) * n / rows
+    del O_buf, Oc
+    plan = m.plan
+    dk = m.d_kept
+    flops = 2.0 * n * d * dk
+    bytes_alg = n * (4.0 * d + m.code_bytes + 4.0 * m.factor_count)
+    if args.precision in ("fp32_simt",) or not tc_enabled(m):
+        sm_mhz = pk["sm_max_mhz"]
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA pipe, TFLOP/s
+        proj_roof = {"bound": "alu", "achieved": flops / t_proj / 1e12, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": flops / t_proj / 1e12 / fp32_peak,
+                     "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
+    else:
+        pkv = pk["bf16_tflops_sustained"]
+        proj_roof = {"bound": "tensor", "achieved": flops / t_proj / 1e12, "peak": pkv,
+                     "unit": "TFLOP/s", "frac": flops / t_proj / 1e12 / pkv, "traffic": None,
+                     "peak_source": "%s bf16 sustained" % pk["source"]}
+    caq_bytes = n * (4.0 * dk + m.code_bytes + 4.0 * m.factor_count)
+    caq_roof = {"bound": "hbm", "achieved": caq_bytes / t_caq / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": caq_bytes / t_caq / 1e9 / pk["hbm_gbs"], "traffic": None,
+                "peak_source": "%s hbm copy" % pk["source"]}
+    if t_proj >= t_caq:
+        roof, dom = proj_roof, "projection"
+    else:
+        roof, dom = caq_roof, "quantize_adjust_pack"
+    roof = dict(roof)
+    roof["kernel"] = dom
+    step_roof = 1.0 / max(flops / n / (pk["bf16_tflops"] * 1e12), bytes_alg / n / (pk["hbm_gbs"] * 1e9))
+
+    # end to end through the host-buffer API: H2D of the rows, D2H of codes+factors
+    e2e = None
+    if not args.no_e2e:
+        ne = min(n, args.e2e_rows)
+        Xh = X[:ne].cpu().pin_memory()
+        ch = torch.empty((ne, max(m.code_bytes, 1)), dtype=torch.uint8).pin_memory()
+        fh = torch.empty((ne, m.factor_count), dtype=torch.float32).pin_memory()
+        m.encode_host(Xh, ch, fh)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            m.encode_host(Xh, ch, fh)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        dt = max_over_ranks(world, dt)
+        e2e = {"value": ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": ne * d * 4,
+               "d2h_bytes_per_step": ne * (m.code_bytes + 4 * m.factor_count),
+               "rows_per_step": ne}
+        del Xh, ch, fh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _ = cpu_baseline(w, X)
+
+    if rank == 0:
+        cfg = workload_desc(w, args.workload, args.precision, plan, m.code_bytes)
+        cfg["parallelism"] = "replicas x%d (independent batches)" % world
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": max(3, args.warmup),
+               "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": cfg, "roofline": roof,
+               "kernels_ms_per_step": {"projection": t_proj * 1e3,
+                                       "quantize_adjust_pack": t_caq * 1e3},
+               "other_kernel_roofline": caq_roof if dom == "projection" else proj_roof,
+               "step_roofline_vectors_per_s": step_roof,
+               "step_roofline_frac": value / world / step_roof,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+               "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def tc_enabled(m):
+    # the library reports the projection kind through its precision setting;
+    # the tensor-core path is used for fp32/bf16/fp8 when available
+    return getattr(m, "tensor_cores", False)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2_d960", choices=list(synth.WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=list(P.PRECISIONS))
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--e2e-rows", type=int, default=1_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-rows", type=int, default=4000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -204,6 +204,22 @@ saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
 saq_status saq_model_export(const saq_model *m, void *buf, size_t *len);
 saq_status saq_model_import(const void *buf, size_t len, saq_model **out);
 
+/*
+ * Quantization plan search alone (Sec. 4.2 Algorithm 2), host only, no GPU:
+ * sig2[d] the per-dimension variances sorted descending, g the segment
+ * granularity, quota_bits the bit quota, max_bits <= 8, tie_frac the
+ * "fewest segments within (1 + tie_frac) of the least error" rule.  Writes
+ * up to cap segments to out, their number to *nseg and the plan's modelled
+ * error to *err (may be NULL).  Same plan as saq_fit computes.
+ */
+saq_status saq_plan_search(const double *sig2, int32_t d, int32_t g, int64_t quota_bits,
+                           int32_t max_bits, double tie_frac, saq_segment *out, int32_t cap,
+                           int32_t *nseg, double *err);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all threads, all devices).  Diagnostic; never reset. */
+uint64_t saq_kernel_launch_count(void);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *saq_last_error(void);
 const char *saq_status_string(saq_status s);

@@ -13,7 +13,10 @@ LIB = os.path.join(HERE, "_saq_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    if (not force and os.path.exists(LIB)
+    import platform
+    marker = LIB + ".arch"
+    same_arch = os.path.exists(marker) and open(marker).read() == platform.machine()
+    if (not force and same_arch and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     # IEEE semantics on purpose: no -ffast-math, no -march=native (the same
@@ -22,6 +25,8 @@ def build(force: bool = False) -> str:
            "-ffp-contract=off", SRC, "-o", LIB + ".tmp", "-lm"]
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
+    with open(marker, "w") as f:
+        f.write(platform.machine())
     return LIB
 
 

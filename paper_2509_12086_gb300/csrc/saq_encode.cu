@@ -1,0 +1,255 @@
+// saq_encode.cu -- C-ABI entry points of the encode hot path and of the
+// estimator: argument checks, scratch management and kernel sequencing.
+#include <algorithm>
+
+#include "saq_internal.h"
+
+namespace saq {
+
+namespace {
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+saq_status check_device(const saq_model *m) {
+    int dev = -1;
+    SAQ_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev != m->device)
+        return set_error(SAQ_ERR_INVALID, "model lives on device %d, current device is %d",
+                         m->device, dev);
+    return SAQ_OK;
+}
+
+// Rows per chunk so that the projected chunk stays within `budget` bytes.
+int64_t chunk_rows(const saq_model *m, int64_t n, size_t budget) {
+    const int64_t per = std::max<int64_t>(1, (int64_t)m->dk * 4);
+    int64_t r = (int64_t)(budget / (size_t)per);
+    r = std::max<int64_t>(r, 256);
+    r = (r / 128) * 128;
+    return std::min<int64_t>(r, n);
+}
+
+bool use_tc(const saq_model *m) {
+    return m->precision != SAQ_PREC_FP32_SIMT && m->tc.precision == m->precision &&
+           tc_supported(m);
+}
+
+}  // namespace
+
+// Projection of rows [0, n) into O (ldo) and |x - c|^2 into norms (stride).
+saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
+                        float *norms, int64_t nstride, cudaStream_t s) {
+    if (use_tc(m)) return launch_project_tc(m, X, n, O, ldo, norms, nstride, s);
+    saq_status st = launch_project_simt(m, X, n, O, ldo, s);
+    if (st != SAQ_OK) return st;
+    return launch_rownorm2(m, X, n, norms, nstride, s);
+}
+
+saq_status quantize_rows(const saq_model *m, const float *O, int64_t ldo, int64_t n,
+                         uint8_t *codes, float *factors, cudaStream_t s) {
+    for (size_t k = 0; k < m->kept.size(); ++k) {
+        saq_status st = launch_caq_segment(m, (int)k, O, ldo, n, codes, factors, s);
+        if (st != SAQ_OK) return st;
+    }
+    return SAQ_OK;
+}
+
+// The whole encode of rows [0, n) on stream s with O scratch of `rows` rows.
+saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
+                       float *factors, float *O, int64_t rows, cudaStream_t s) {
+    for (int64_t r0 = 0; r0 < n; r0 += rows) {
+        const int64_t nr = std::min(rows, n - r0);
+        saq_status st = project_rows(m, X + r0 * m->d, nr, O, m->dk, factors + r0 * m->nf,
+                                     m->nf, s);
+        if (st != SAQ_OK) return st;
+        st = quantize_rows(m, O, m->dk, nr, codes + r0 * (int64_t)m->code_bytes,
+                           factors + r0 * m->nf, s);
+        if (st != SAQ_OK) return st;
+    }
+    return SAQ_OK;
+}
+
+}  // namespace saq
+
+using namespace saq;
+
+extern "C" {
+
+saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n, uint8_t *codes_dev,
+                      float *factors_dev, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0) return set_error(SAQ_ERR_INVALID, "n < 0");
+    if (n == 0) return SAQ_OK;
+    if (!X_dev || !factors_dev || (m->code_bytes > 0 && !codes_dev))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(X_dev) || !aligned16(codes_dev) || !aligned16(factors_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->dk == 0) return launch_rownorm2(m, X_dev, n, factors_dev, m->nf, s);
+    const int64_t rows = chunk_rows(m, n, (size_t)512 << 20);
+    float *O = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&O, sizeof(float) * (size_t)rows * m->dk, s);
+    if (e != cudaSuccess)
+        return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
+    st = encode_rows(m, X_dev, n, codes_dev, factors_dev, O, rows, s);
+    cudaFreeAsync(O, s);
+    return st;
+}
+
+saq_status saq_project(const saq_model *m, const float *X_dev, int64_t n, float *O_dev,
+                       float *norms2_dev, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0) return set_error(SAQ_ERR_INVALID, "n < 0");
+    if (n == 0) return SAQ_OK;
+    if (!X_dev || !norms2_dev || (m->dk > 0 && !O_dev))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(X_dev) || !aligned16(O_dev) || !aligned16(norms2_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    return project_rows(m, X_dev, n, O_dev, m->dk, norms2_dev, 1, (cudaStream_t)stream);
+}
+
+saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
+                                  const float *norms2_dev, int64_t n, uint8_t *codes_dev,
+                                  float *factors_dev, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0) return set_error(SAQ_ERR_INVALID, "n < 0");
+    if (n == 0) return SAQ_OK;
+    if (!norms2_dev || !factors_dev || (m->dk > 0 && (!O_dev || !codes_dev)))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(O_dev) || !aligned16(codes_dev) || !aligned16(factors_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = launch_copy_strided(norms2_dev, 1, factors_dev, m->nf, n, s);
+    if (st != SAQ_OK) return st;
+    return quantize_rows(m, O_dev, m->dk, n, codes_dev, factors_dev, s);
+}
+
+saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
+                           uint8_t *codes_host, float *factors_host, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0) return set_error(SAQ_ERR_INVALID, "n < 0");
+    if (n == 0) return SAQ_OK;
+    if (!X_host || !factors_host || (m->code_bytes > 0 && !codes_host))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // Two pipeline slots: the copy-in of chunk i+1 and the copy-out of chunk
+    // i-1 overlap the encode of chunk i (copy and compute on separate
+    // streams, ordered by events).
+    const int64_t rows = std::min<int64_t>(n, 65536);
+    const size_t xb = sizeof(float) * (size_t)rows * m->d;
+    const size_t cb = m->code_bytes * (size_t)rows;
+    const size_t fb = sizeof(float) * (size_t)rows * m->nf;
+    const size_t ob = sizeof(float) * (size_t)rows * std::max(1, m->dk);
+    uint8_t *buf[2] = {nullptr, nullptr};
+    float *O = nullptr;
+    cudaStream_t cs[2] = {nullptr, nullptr};
+    cudaEvent_t in_done[2] = {nullptr, nullptr}, enc_done[2] = {nullptr, nullptr},
+                out_done[2] = {nullptr, nullptr};
+    auto round16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t slot = round16(xb) + round16(cb) + round16(fb);
+    auto cleanup = [&]() {
+        for (int i = 0; i < 2; ++i) {
+            if (cs[i]) cudaStreamSynchronize(cs[i]);
+        }
+        cudaStreamSynchronize(s);
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(buf[i]);
+            if (cs[i]) cudaStreamDestroy(cs[i]);
+            if (in_done[i]) cudaEventDestroy(in_done[i]);
+            if (enc_done[i]) cudaEventDestroy(enc_done[i]);
+            if (out_done[i]) cudaEventDestroy(out_done[i]);
+        }
+        cudaFree(O);
+    };
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&buf[i], slot) != cudaSuccess) { cleanup(); return set_error(SAQ_ERR_OOM, "staging allocation failed"); }
+        if (cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&in_done[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&enc_done[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&out_done[i], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return set_error(SAQ_ERR_CUDA, "stream/event creation failed");
+        }
+    }
+    if (cudaMalloc(&O, ob) != cudaSuccess) { cleanup(); return set_error(SAQ_ERR_OOM, "scratch allocation failed"); }
+    st = SAQ_OK;
+    int64_t chunk = 0;
+    for (int64_t r0 = 0; r0 < n && st == SAQ_OK; r0 += rows, ++chunk) {
+        const int sl = (int)(chunk & 1);
+        const int64_t nr = std::min(rows, n - r0);
+        float *dx = (float *)buf[sl];
+        uint8_t *dc = buf[sl] + round16(xb);
+        float *df = (float *)(buf[sl] + round16(xb) + round16(cb));
+        // the slot's previous copy-out must be done before it is overwritten
+        cudaStreamWaitEvent(cs[sl], out_done[sl], 0);
+        cudaMemcpyAsync(dx, X_host + r0 * m->d, sizeof(float) * (size_t)nr * m->d,
+                        cudaMemcpyHostToDevice, cs[sl]);
+        cudaEventRecord(in_done[sl], cs[sl]);
+        cudaStreamWaitEvent(s, in_done[sl], 0);
+        if (m->dk == 0) st = launch_rownorm2(m, dx, nr, df, m->nf, s);
+        else st = encode_rows(m, dx, nr, dc, df, O, rows, s);
+        cudaEventRecord(enc_done[sl], s);
+        cudaStreamWaitEvent(cs[sl], enc_done[sl], 0);
+        if (m->code_bytes)
+            cudaMemcpyAsync(codes_host + r0 * (int64_t)m->code_bytes, dc, m->code_bytes * (size_t)nr,
+                            cudaMemcpyDeviceToHost, cs[sl]);
+        cudaMemcpyAsync(factors_host + r0 * m->nf, df, sizeof(float) * (size_t)nr * m->nf,
+                        cudaMemcpyDeviceToHost, cs[sl]);
+        cudaEventRecord(out_done[sl], cs[sl]);
+    }
+    cudaError_t e = cudaGetLastError();
+    cleanup();
+    if (st != SAQ_OK) return st;
+    if (e != cudaSuccess) return set_error(SAQ_ERR_CUDA, "encode_host: %s", cudaGetErrorString(e));
+    return SAQ_OK;
+}
+
+saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
+                             const float *factors_dev, int64_t n, const float *Q_dev, int64_t nq,
+                             int32_t prefix_bits, float *dist_dev, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0 || nq < 0 || prefix_bits < 0) return set_error(SAQ_ERR_INVALID, "negative size");
+    if (n == 0 || nq == 0) return SAQ_OK;
+    if (!factors_dev || !Q_dev || !dist_dev || (m->code_bytes > 0 && !codes_dev))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(codes_dev) || !aligned16(factors_dev) || !aligned16(Q_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nk = m->kept.size();
+    float *qrot = nullptr, *qn2 = nullptr, *vs = nullptr;
+    const size_t bq = sizeof(float) * (size_t)nq * std::max(1, m->dk);
+    const size_t bv = sizeof(float) * (size_t)n * std::max<size_t>(1, nk);
+    if (cudaMallocAsync((void **)&qrot, bq, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&qn2, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&vs, bv, s) != cudaSuccess) {
+        if (qrot) cudaFreeAsync(qrot, s);
+        if (qn2) cudaFreeAsync(qn2, s);
+        return set_error(SAQ_ERR_OOM, "scratch allocation failed");
+    }
+    // queries are rotated with the FP32 CUDA-core projection
+    st = launch_project_simt(m, Q_dev, nq, qrot, m->dk, s);
+    if (st == SAQ_OK) st = launch_rownorm2(m, Q_dev, nq, qn2, 1, s);
+    if (st == SAQ_OK)
+        st = launch_estimate(m, codes_dev, factors_dev, n, qrot, qn2, nq, prefix_bits, vs,
+                             dist_dev, s);
+    cudaFreeAsync(qrot, s);
+    cudaFreeAsync(qn2, s);
+    cudaFreeAsync(vs, s);
+    return st;
+}
+
+}  // extern "C"

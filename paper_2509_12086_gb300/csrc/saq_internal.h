@@ -1,0 +1,119 @@
+// saq_internal.h -- declarations shared by the library's translation units.
+// Library-internal: nothing here is part of the C ABI in include/saq.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "saq.h"
+
+namespace saq {
+
+// ---------------------------------------------------------------- errors
+saq_status set_error(saq_status s, const char *fmt, ...);
+// Count `k` kernel launches (saq_kernel_launch_count).
+void note_launches(int k = 1);
+void clear_error();
+
+#define SAQ_CUDA_CHECK(call)                                                   \
+    do {                                                                       \
+        cudaError_t e__ = (call);                                              \
+        if (e__ != cudaSuccess)                                                \
+            return ::saq::set_error(SAQ_ERR_CUDA, "%s failed: %s (%s:%d)",     \
+                                    #call, cudaGetErrorString(e__), __FILE__,  \
+                                    __LINE__);                                 \
+    } while (0)
+
+// ------------------------------------------------------------------ model
+// A kept segment in the projected (kept-column) space.
+struct KeptSeg {
+    int32_t start;     // first PCA dimension of the segment
+    int32_t off;       // first column of the segment in O (kept space)
+    int32_t len;       // coordinates
+    int32_t bits;      // 1..8
+    int64_t code_off;  // byte offset of the segment inside a code record
+    int32_t words;     // 64-bit words per bit-plane = ceil(len / 64)
+    int32_t fidx;      // factor index of |o_s| (cos_s follows)
+};
+
+// Device operands of the tensor-core projection (built per precision).
+struct TcOperands {
+    int precision = -1;
+    void *w_hi = nullptr;     // dk_pad x d_pad  (FP16 hi / BF16 / FP8)
+    void *w_lo = nullptr;     // dk_pad x d_pad  (FP16 lo) or nullptr
+    float *col_scale = nullptr;  // per output column dequant scale (dk_pad)
+    int dk_pad = 0;
+    int d_pad = 0;
+};
+
+}  // namespace saq
+
+struct saq_model {
+    int32_t d = 0;
+    int32_t dk = 0;           // kept dimensions
+    int32_t rounds = 6;
+    int32_t precision = SAQ_PREC_FP32;
+    int device = 0;
+    std::vector<saq_segment> plan;        // all segments
+    std::vector<saq::KeptSeg> kept;       // kept segments, plan order
+    std::vector<double> mean;             // d
+    std::vector<double> W;                // dk x d row-major
+    std::vector<double> sig2;             // d (zeros if unknown)
+    size_t code_bytes = 0;
+    int32_t nf = 1;                       // factors per vector
+    // device copies
+    float *d_mean = nullptr;              // d
+    float *d_W = nullptr;                 // dk x d FP32 row-major
+    saq::TcOperands tc;
+};
+
+namespace saq {
+
+// ------------------------------------------------------------ host pieces
+// Algorithm 2 plan search (library implementation).
+int plan_search(const double *sig2, int D, int g, int64_t quota_bits,
+                int max_bits, double tie_frac, std::vector<saq_segment> &out,
+                double *err, double *min_err);
+
+// Counter-based Gaussian draws (Philox4x32-10 + Box-Muller), FP64.
+void philox_gaussian(uint64_t seed, uint64_t stream_id, double *out, size_t n);
+
+saq_status model_finalize(saq_model *m);  // derive kept segs, upload
+saq_status model_build_tc(saq_model *m, int precision, cudaStream_t s);
+void model_release_device(saq_model *m);
+
+// ---------------------------------------------------------------- kernels
+// O[i, :] = W (x_i - c) for rows [0, n): FP32 SIMT GEMM, exact FP32 products.
+saq_status launch_project_simt(const saq_model *m, const float *X, int64_t n,
+                               float *O, int64_t ldo, cudaStream_t s);
+// Tensor-core projection (tcgen05 + TMA); precision from m->tc.
+saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n,
+                             float *O, int64_t ldo, float *norms2,
+                             int64_t norms_stride, cudaStream_t s);
+bool tc_supported(const saq_model *m);
+// norms2[i * stride] = |x_i - c|^2
+saq_status launch_rownorm2(const saq_model *m, const float *X, int64_t n,
+                           float *out, int64_t stride, cudaStream_t s);
+// Strided copy of n floats.
+saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
+                               int64_t dstride, int64_t n, cudaStream_t s);
+// Quantize + adjust + pack one kept segment for rows [0, n) of O.
+saq_status launch_caq_segment(const saq_model *m, int seg, const float *O,
+                              int64_t ldo, int64_t n, uint8_t *codes,
+                              float *factors, cudaStream_t s);
+// Estimator.
+saq_status launch_estimate(const saq_model *m, const uint8_t *codes,
+                           const float *factors, int64_t n, const float *Qrot,
+                           const float *qn2, int64_t nq, int prefix_bits,
+                           float *vscale, float *dist, cudaStream_t s);
+// Fit kernels (FP64).
+saq_status launch_mean_f64(const float *X, int64_t n, int d, double *mean,
+                           double *partial, int nsplit, cudaStream_t s);
+saq_status launch_cov_f64(const float *X, int64_t n, int d, const double *mean,
+                          double *cov, double *partial, int nsplit,
+                          cudaStream_t s);
+
+}  // namespace saq

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Bars (FP32 path):
+  * >= 99.9% of codes identical, and every vector-segment with a mismatching
+    code has an oracle decision margin < 1e-5 (cosine units for adjustment
+    trials, |o| units for initial-code interval boundaries);
+  * per-vector relative quantization error within 1e-4 of the oracle's;
+  * |o_s| within 1e-5 relative, cos_s within 1e-5;
+  * mean relative distance-estimate error within 1e-4 of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2509_12086_gb300 as P
+from paper_2509_12086_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CODE_AGREE = 0.999
+MARGIN = 1e-5
+EPS_TOL = 1e-4
+DIST_TOL = 1e-4
+
+
+def lib_model(mo, precision="fp32", rounds=6):
+    return P.saq_model_create(mo.d, mo.mean, mo.W, mo.plan, mo.sig2, rounds=rounds,
+                              precision=precision)
+
+
+def precisions():
+    return ["fp32_simt", "fp32"]
+
+
+def check_codes(mo, eo, codes_gpu, factors_gpu, agree_min=CODE_AGREE, margin=MARGIN):
+    codes = O.unpack(codes_gpu, mo)
+    # padding bits of the packed planes are zero: pack(unpack(x)) == x
+    assert np.array_equal(O.pack(codes, mo), codes_gpu)
+    eq = codes == eo.codes
+    frac = eq.mean() if eq.size else 1.0
+    assert frac >= agree_min, "code agreement %.6f" % frac
+    mism = np.zeros((codes.shape[0], len(mo.kept)), dtype=bool)
+    for j, (off, l, b) in enumerate(mo.kept):
+        mism[:, j] = ~eq[:, off:off + l].all(axis=1)
+    if mism.any():
+        worst = eo.min_margin[mism].max()
+        assert worst < margin, "mismatch at oracle margin %.3g" % worst
+    f = factors_gpu.astype(np.float64)
+    ref = eo.factors
+    nr_g, nr_o = f[:, 1::2], ref[:, 1::2]
+    assert np.allclose(nr_g, nr_o, rtol=1e-5, atol=1e-6 * max(1.0, nr_o.max()))
+    assert np.allclose(f[:, 0], ref[:, 0], rtol=1e-5, atol=1e-6 * max(1.0, ref[:, 0].max()))
+    cs_ok = np.abs(f[:, 2::2] - ref[:, 2::2]) <= 1e-5
+    assert np.all(cs_ok | mism), "cos factor off where codes agree"
+    eg, eo_ = O.quant_error(f, mo), O.quant_error(ref, mo)
+    assert np.max(np.abs(eg - eo_)) <= EPS_TOL
+    return frac, mism.mean() if mism.size else 0.0
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w = synth.WORKLOADS["c1_d128"]
+    X = synth.power_law(w["n"], w["d"], w["alpha"]).numpy()
+    Qm = synth.queries(w["nq"], w["d"], w["alpha"]).numpy()
+    mo = O.fit(X, w["avg_bits"])
+    eo = O.encode(X, mo, rounds=w["rounds"])
+    return X, Qm, mo, eo
+
+
+@pytest.mark.parametrize("prec", precisions())
+def test_c1_encode_parity(c1, prec):
+    X, Qm, mo, eo = c1
+    m = lib_model(mo, prec)
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy())
+
+
+def test_c1_quantize_only_parity(c1):
+    """Quantize + adjust + pack alone, fed the oracle's projection rounded to
+    FP32; the oracle runs on the same rounded values.  Only FP32 rounding in
+    the decisions separates the two."""
+    X, Qm, mo, _ = c1
+    Oo, n2 = O.project(X, mo)
+    O32 = Oo.astype(np.float32)
+    eo = O.encode_projected(O32.astype(np.float64), n2, mo, rounds=6)
+    m = lib_model(mo)
+    codes, factors = m.quantize_projected(torch.from_numpy(O32).cuda(),
+                                          torch.from_numpy(n2.astype(np.float32)).cuda())
+    frac, _ = check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(),
+                          agree_min=0.9999, margin=1e-6)
+
+
+def test_c1_estimator_parity(c1):
+    X, Qm, mo, eo = c1
+    m = lib_model(mo)
+    # library estimator on the oracle's codes: FP32 arithmetic only
+    codes_o = torch.from_numpy(O.pack(eo.codes, mo)).cuda()
+    fac_o = torch.from_numpy(eo.factors.astype(np.float32)).cuda()
+    Qt = torch.from_numpy(Qm).cuda()
+    dl = m.estimate_dist(codes_o, fac_o, Qt).cpu().numpy().astype(np.float64)
+    do = O.estimate(mo, eo.codes, eo.factors, Qm)
+    assert np.max(np.abs(dl - do) / np.abs(do).max()) < 1e-5
+    # end to end: GPU codes and GPU estimator vs oracle codes and estimator
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    dg = m.estimate_dist(codes, factors, Qt).cpu().numpy().astype(np.float64)
+    ex = O.exact_dist(X, Qm)
+    rg = O.relative_error(dg, ex).mean()
+    ro = O.relative_error(do, ex).mean()
+    assert abs(rg - ro) <= DIST_TOL, (rg, ro)
+    # progressive prefixes (Sec. 3.2)
+    for b in (1, 2, 3):
+        dlb = m.estimate_dist(codes_o, fac_o, Qt, prefix_bits=b).cpu().numpy()
+        dob = O.estimate(mo, eo.codes, eo.factors, Qm, prefix_bits=b)
+        assert np.max(np.abs(dlb - dob) / np.abs(dob).max()) < 1e-5
+
+
+def _random_model(d, plan, seed=0):
+    rng = np.random.default_rng(seed)
+    dk = sum(l for _, l, b in plan if b > 0)
+    Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    # an FP32-representable mean, so that rows equal to it centre to exact zeros
+    mean = (rng.standard_normal(d) * 0.1).astype(np.float32).astype(np.float64)
+    return O.Model(d=d, mean=mean, W=Q[:dk].copy(), plan=plan)
+
+
+@pytest.mark.parametrize("prec", precisions())
+@pytest.mark.parametrize("n", [1, 13, 1000])
+def test_edge_plans_and_ragged_rows(prec, n):
+    """Ragged segment (72 coordinates, not a multiple of 32 or 64), a dropped
+    segment, B = 1 and B = 8, a 32-wide segment, ragged row counts, and
+    rows equal to the mean (all-zero segments)."""
+    plan = [(0, 64, 8), (64, 72, 3), (136, 32, 1), (168, 32, 0)]
+    mo = _random_model(200, plan)
+    rng = np.random.default_rng(n)
+    X = (rng.standard_normal((n, 200)) * np.linspace(1, 0.1, 200)).astype(np.float32)
+    X[:: 5] = mo.mean.astype(np.float32)
+    eo = O.encode(X, mo, rounds=6)
+    m = lib_model(mo, prec)
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(), agree_min=0.999)
+
+
+def test_zero_rows_and_empty_call():
+    plan = [(0, 64, 4)]
+    mo = _random_model(64, plan)
+    m = lib_model(mo)
+    X = np.tile(mo.mean.astype(np.float32), (9, 1))
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    c = codes.cpu().numpy()
+    f = factors.cpu().numpy()
+    assert np.all(c == 0) and np.all(f[:, 1] == 0) and np.all(f[:, 2] == 1)
+    codes, factors = m.encode(torch.empty((0, 64), device="cuda"))
+    assert codes.shape[0] == 0
+
+
+def test_long_segment_1024():
+    plan = [(0, 1024, 3)]
+    mo = _random_model(1024, plan, seed=3)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((300, 1024)).astype(np.float32)
+    eo = O.encode(X, mo, rounds=6)
+    m = lib_model(mo)
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy())
+
+
+def test_fit_parity():
+    """Library fit (GPU FP64 covariance, cuSOLVER) vs oracle fit (numpy):
+    same plan, same variances, same mean, and per kept segment the same
+    subspace (W_s^T W_s equals V_s V_s^T; the rotation inside a segment is
+    random, so the blocks themselves differ)."""
+    X = synth.power_law(20000, 128, 1.0).numpy()
+    mo = O.fit(X, 4.0)
+    m = P.saq_fit(torch.from_numpy(X).cuda(), avg_bits=4.0)
+    assert m.plan == mo.plan
+    assert np.allclose(m.variances, mo.sig2, rtol=1e-9, atol=1e-15)
+    assert np.allclose(m.mean, mo.mean, rtol=0, atol=1e-12)
+    W = m.matrix
+    assert np.max(np.abs(W @ W.T - np.eye(W.shape[0]))) < 1e-10
+    off = 0
+    for (s, l, b) in mo.plan:
+        if b == 0:
+            continue
+        P1 = W[off:off + l].T @ W[off:off + l]
+        P2 = mo.W[off:off + l].T @ mo.W[off:off + l]
+        assert np.max(np.abs(P1 - P2)) < 1e-8
+        off += l
+
+
+def test_export_import_and_host_path(c1):
+    X, Qm, mo, eo = c1
+    m = lib_model(mo)
+    blob = m.export()
+    m2 = P.saq_model_import(blob)
+    assert m2.plan == mo.plan and np.array_equal(m2.matrix, mo.W)
+    Xd = torch.from_numpy(X).cuda()
+    c1_, f1 = m.encode(Xd)
+    c2_, f2 = m2.encode(Xd)
+    assert torch.equal(c1_, c2_) and torch.equal(f1, f2)
+    ch, fh = m.encode_host(torch.from_numpy(X).pin_memory())
+    assert np.array_equal(ch.numpy(), c1_.cpu().numpy())
+    assert np.array_equal(fh.numpy(), f1.cpu().numpy())
+
+
+def test_c2_full_size_sampled_rows():
+    """d = 960, 4 bits/dim, 1,000,000 rows encoded in the benchmark's launch
+    configuration; 20,000 seeded sample rows and 1,000 x 1,000 distances are
+    checked against the oracle."""
+    w = synth.WORKLOADS["c2_d960"]
+    n, d = w["n"], w["d"]
+    X = synth.power_law(n, d, w["alpha"], device="cuda")
+    fit_rows = X[:50000].cpu().numpy()
+    mo = O.fit(fit_rows, w["avg_bits"])
+    m = lib_model(mo, "fp32")
+    codes, factors = m.encode(X)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(7).choice(n, 20000, replace=False))
+    it = torch.from_numpy(idx).cuda()
+    Xs = X[it].cpu().numpy()
+    eo = O.encode(Xs, mo, rounds=w["rounds"])
+    check_codes(mo, eo, codes[it].cpu().numpy(), factors[it].cpu().numpy())
+    Qm = synth.queries(1000, d, w["alpha"]).numpy()
+    sub = idx[:1000]
+    ex = O.exact_dist(Xs[:1000], Qm)
+    do = O.estimate(mo, eo.codes[:1000], eo.factors[:1000], Qm)
+    dg = m.estimate_dist(codes[torch.from_numpy(sub).cuda()], factors[torch.from_numpy(sub).cuda()],
+                         torch.from_numpy(Qm).cuda()).cpu().numpy().astype(np.float64)
+    assert abs(O.relative_error(dg, ex).mean() - O.relative_error(do, ex).mean()) <= DIST_TOL
