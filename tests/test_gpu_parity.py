@@ -35,13 +35,23 @@ def precisions():
 
 
 def check_codes(mo, eo, codes_gpu, factors_gpu, agree_min=CODE_AGREE, margin=MARGIN):
+    """Codes and factors against the oracle.
+
+    Where a vector-segment's codes all agree, its factors must agree tightly.
+    A vector-segment with a mismatch must have an oracle decision margin below
+    `margin` (a near-tie that FP32 may resolve the other way); past such a
+    decision both trajectories are correct CAQ results, so there the GPU
+    result is checked for validity instead: its cosine is at least the
+    initial code's and within 1e-3 of the oracle's.  The per-vector error
+    bar applies to every vector without an excused mismatch."""
     codes = O.unpack(codes_gpu, mo)
     # padding bits of the packed planes are zero: pack(unpack(x)) == x
     assert np.array_equal(O.pack(codes, mo), codes_gpu)
     eq = codes == eo.codes
     frac = eq.mean() if eq.size else 1.0
     assert frac >= agree_min, "code agreement %.6f" % frac
-    mism = np.zeros((codes.shape[0], len(mo.kept)), dtype=bool)
+    k = len(mo.kept)
+    mism = np.zeros((codes.shape[0], k), dtype=bool)
     for j, (off, l, b) in enumerate(mo.kept):
         mism[:, j] = ~eq[:, off:off + l].all(axis=1)
     if mism.any():
@@ -52,10 +62,15 @@ def check_codes(mo, eo, codes_gpu, factors_gpu, agree_min=CODE_AGREE, margin=MAR
     nr_g, nr_o = f[:, 1::2], ref[:, 1::2]
     assert np.allclose(nr_g, nr_o, rtol=1e-5, atol=1e-6 * max(1.0, nr_o.max()))
     assert np.allclose(f[:, 0], ref[:, 0], rtol=1e-5, atol=1e-6 * max(1.0, ref[:, 0].max()))
-    cs_ok = np.abs(f[:, 2::2] - ref[:, 2::2]) <= 1e-5
-    assert np.all(cs_ok | mism), "cos factor off where codes agree"
+    cg, co = f[:, 2::2], ref[:, 2::2]
+    assert np.all((np.abs(cg - co) <= 1e-5) | mism), "cos factor off where codes agree"
+    if mism.any():
+        assert np.all(cg[mism] >= eo.init_cos[mism] - 1e-6)
+        assert np.all(np.abs(cg[mism] - co[mism]) <= 1e-3)
+    clean = ~mism.any(axis=1)
     eg, eo_ = O.quant_error(f, mo), O.quant_error(ref, mo)
-    assert np.max(np.abs(eg - eo_)) <= EPS_TOL
+    assert np.max(np.abs(eg - eo_)[clean], initial=0.0) <= EPS_TOL
+    assert abs(eg.mean() - eo_.mean()) <= EPS_TOL
     return frac, mism.mean() if mism.size else 0.0
 
 
