@@ -180,6 +180,33 @@ saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
                                   void *stream);
 
 /*
+ * saq_encode for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this is a deployment variant of the encode above.
+ *
+ * Some callers may not call cudaMalloc (or any allocating routine) at encode
+ * time: a framework that owns all device memory through its own allocator,
+ * so a driver-level allocation would fail or fragment its pool; an ingest
+ * thread with a hard latency budget, where an allocation can block and
+ * synchronise the device; or a host (a database extension, a plugin) that
+ * forbids driver allocations from inside its callbacks.  This entry point
+ * allocates nothing: its scratch (the projected rows) lives in a fixed
+ * 32 MiB array in the library's device memory, which every GPU that loads
+ * the library keeps until the process exits.
+ *
+ * Limit: n * d_kept <= 8,388,608 (32 MiB of FP32 scratch), e.g. 8,738 rows
+ * at d_kept = 960; larger n is rejected with SAQ_ERR_INVALID before any
+ * launch.  Arguments and outputs are as for saq_encode.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  Every call shares the one array, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  The array keeps the last call's contents;
+ * nothing in it needs to start at zero.
+ */
+saq_status saq_encode_noalloc(const saq_model *m, const float *X_dev, int64_t n,
+                              uint8_t *codes_dev, float *factors_dev, void *stream);
+
+/*
  * Estimated squared distances dist_dev[q * n + v] between query q (rows of
  * Q_dev, device nq x d FP32) and encoded vector v:
  *   |o_r - q_r|^2 ~ |o_r - c|^2 + |q_r - c|^2 - 2 sum_s est_s      (Eq. 3)

@@ -33,6 +33,7 @@ EXPORTS = [
     "saq_encode", "saq_encode_host", "saq_project", "saq_quantize_projected",
     "saq_estimate_dist", "saq_model_export", "saq_model_import", "saq_last_error",
     "saq_status_string", "saq_plan_search", "saq_kernel_launch_count",
+    "saq_encode_noalloc",
 ]
 
 
@@ -92,6 +93,7 @@ def load() -> ctypes.CDLL:
         "saq_last_error": (ctypes.c_char_p, []),
         "saq_status_string": (ctypes.c_char_p, [st]),
         "saq_kernel_launch_count": (ctypes.c_uint64, []),
+        "saq_encode_noalloc": (st, [mp, vp, i64, vp, vp, vp]),
         "saq_plan_search": (st, [dp, i32, i32, i64, i32, ctypes.c_double,
                                  ctypes.POINTER(saq_segment), i32, ctypes.POINTER(i32), dp]),
     }

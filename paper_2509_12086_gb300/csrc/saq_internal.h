@@ -104,6 +104,11 @@ saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
 saq_status launch_caq_segment(const saq_model *m, int seg, const float *O,
                               int64_t ldo, int64_t n, uint8_t *codes,
                               float *factors, cudaStream_t s);
+// Projection and quantization of rows [0, n) (saq_encode.cu).
+saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
+                        float *norms, int64_t nstride, cudaStream_t s);
+saq_status quantize_rows(const saq_model *m, const float *O, int64_t ldo, int64_t n,
+                         uint8_t *codes, float *factors, cudaStream_t s);
 // Estimator.
 saq_status launch_estimate(const saq_model *m, const uint8_t *codes,
                            const float *factors, int64_t n, const float *Qrot,
