@@ -313,7 +313,7 @@ def run_ours(args):
 def tc_enabled(m):
     # the library reports the projection kind through its precision setting;
     # the tensor-core path is used for fp32/bf16/fp8 when available
-    return getattr(m, "tensor_cores", False)
+    return m.tensor_cores
 
 
 def main():

@@ -243,6 +243,15 @@ saq_status saq_plan_search(const double *sig2, int32_t d, int32_t g, int64_t quo
                            int32_t max_bits, double tie_frac, saq_segment *out, int32_t cap,
                            int32_t *nseg, double *err);
 
+/* 1 if the model's projection runs on the tensor cores (tcgen05), 0 if on
+ * the CUDA cores (SAQ_PREC_FP32_SIMT, or d not a multiple of 4). */
+int32_t saq_model_uses_tensor_cores(const saq_model *m);
+
+/* Synchronise `stream`, then report whether a bounded device wait inside the
+ * model's kernels gave up since the last check (SAQ_ERR_TIMEOUT; the flag is
+ * cleared).  Failure detection for the asynchronous entry points. */
+saq_status saq_check_device(const saq_model *m, void *stream);
+
 /* Number of CUDA kernels the library has launched in this process so far
  * (all threads, all devices).  Diagnostic; never reset. */
 uint64_t saq_kernel_launch_count(void);

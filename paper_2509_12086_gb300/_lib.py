@@ -33,7 +33,7 @@ EXPORTS = [
     "saq_encode", "saq_encode_host", "saq_project", "saq_quantize_projected",
     "saq_estimate_dist", "saq_model_export", "saq_model_import", "saq_last_error",
     "saq_status_string", "saq_plan_search", "saq_kernel_launch_count",
-    "saq_encode_noalloc",
+    "saq_encode_noalloc", "saq_model_uses_tensor_cores", "saq_check_device",
 ]
 
 
@@ -94,6 +94,8 @@ def load() -> ctypes.CDLL:
         "saq_status_string": (ctypes.c_char_p, [st]),
         "saq_kernel_launch_count": (ctypes.c_uint64, []),
         "saq_encode_noalloc": (st, [mp, vp, i64, vp, vp, vp]),
+        "saq_model_uses_tensor_cores": (i32, [mp]),
+        "saq_check_device": (st, [mp, vp]),
         "saq_plan_search": (st, [dp, i32, i32, i64, i32, ctypes.c_double,
                                  ctypes.POINTER(saq_segment), i32, ctypes.POINTER(i32), dp]),
     }
@@ -194,6 +196,14 @@ class Model:
         out = np.zeros(self.d)
         _check(load().saq_model_get_variances(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
+
+    @property
+    def tensor_cores(self) -> bool:
+        return bool(load().saq_model_uses_tensor_cores(self._h))
+
+    def check_device(self, stream=None):
+        """Synchronise and raise if a bounded device wait gave up."""
+        _check(load().saq_check_device(self._h, _stream(stream)))
 
     def set_precision(self, precision):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)

@@ -1,17 +1,625 @@
-// k_tc.cu -- tensor-core projection (tcgen05 + TMA).  Not yet enabled.
+// k_tc.cu -- tensor-core projection O = (X - c) W^T on sm_103a (Sec. 3.1
+// Eq. rotate with the combined PCA + segment-rotation matrix of Sec. 5.1).
+//
+// One CTA computes a 128-row x 128-column tile of O over the full K = d:
+//   warp 0      TMA producer: X tile (FP32, 128 x BK, 128-byte swizzle,
+//               staged) and the W operand tile(s) for the stage;
+//   warp 1      TMEM owner and MMA issuer (one elected lane): tcgen05.mma
+//               with the accumulator (128 lanes x 128 FP32 columns) in TMEM;
+//   warps 2-5   converters, then epilogue.  Thread <-> tile row: the thread
+//               reads its row of the staged X tile, centres it (x - c),
+//               converts it into the A operand(s) in the UMMA K-major
+//               128-byte-swizzled layout, and accumulates |x - c|^2; after the
+//               K loop it reads its accumulator row back with tcgen05.ld.
+// Precision modes:
+//   kSplit  FP32: A = a_hi + a_lo and B = b_hi + b_lo as FP16 pairs (scaled by
+//           powers of two), D = a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32
+//           accumulation (error of the order of FP32 rounding);
+//   kBF16   one BF16 product;
+//   kFP8    one E4M3 product (kind::f8f6f4), per-segment scales on W.
+// All waits are bounded (about 2 s); a timed-out wait raises an error flag,
+// every role leaves its loop, in-flight copies and MMAs are drained, TMEM is
+// freed and the kernel returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <math.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "saq_internal.h"
 
 namespace saq {
 
-bool tc_supported(const saq_model *) { return false; }
+namespace {
 
-saq_status model_build_tc(saq_model *, int, cudaStream_t) {
-    return set_error(SAQ_ERR_UNSUPPORTED, "tensor-core projection not built");
+enum Mode { kSplit = 0, kBF16 = 1, kFP8 = 2 };
+
+constexpr int kBM = 128;           // rows per tile (UMMA M)
+constexpr int kNP = 128;           // output columns per tile (UMMA N)
+constexpr int kTmemCols = 128;
+constexpr int kThreads = 192;
+constexpr uint32_t kTile = 16384;  // one 128 x 128-byte operand / staging tile
+
+template <int MODE> struct Cfg;
+template <> struct Cfg<kSplit> {
+    static constexpr int BK = 64, STAGES = 2, NA = 2, XBOX = 2;
+};
+template <> struct Cfg<kBF16> {
+    static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2;
+};
+template <> struct Cfg<kFP8> {
+    static constexpr int BK = 128, STAGES = 2, NA = 1, XBOX = 4;
+};
+
+template <int MODE> constexpr uint32_t stage_bytes() {
+    return (uint32_t)(Cfg<MODE>::XBOX + 2 * Cfg<MODE>::NA) * kTile;
+}
+template <int MODE> constexpr uint32_t smem_bytes() {
+    return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 /*align*/ + 256 /*barriers*/;
 }
 
-saq_status launch_project_tc(const saq_model *, const float *, int64_t, float *, int64_t,
-                             float *, int64_t, cudaStream_t) {
-    return set_error(SAQ_ERR_UNSUPPORTED, "tensor-core projection not built");
+// ------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+// Bounded wait for the phase of `parity` to complete.  Returns false on a
+// timeout (after raising the flags) or when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err, int code) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0u) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > kWaitNs) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+template <int MODE> __device__ __forceinline__ constexpr uint32_t umma_idesc() {
+    uint32_t d = 1u << 4;                           // accumulate in FP32
+    if (MODE == kBF16) d |= (1u << 7) | (1u << 10);  // A, B = BF16 (F16 and E4M3 encode as 0)
+    d |= (uint32_t)(kNP >> 3) << 17;
+    d |= (uint32_t)(kBM >> 4) << 24;
+    return d;
+}
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t acc) {
+    if (MODE == kFP8) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
+__device__ __forceinline__ uint32_t pack_b2(__nv_bfloat162 h) {
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Offset of 16-byte chunk `c` of row `r` in a 128-row x 128-byte tile with
+// the 128-byte swizzle (chunk index XOR row mod 8).
+__device__ __forceinline__ uint32_t swz(int r, int c) {
+    return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmb0,
+          const __grid_constant__ CUtensorMap tmb1, int64_t n, int dk, int npass, int nkb,
+          const float *__restrict__ mean_pad, float x_scale, const float *__restrict__ col_scale,
+          float *__restrict__ O, int64_t ldo, float *__restrict__ norms, int64_t nstride,
+          int *__restrict__ err) {
+    using C = Cfg<MODE>;
+    constexpr uint32_t SB = stage_bytes<MODE>();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + C::STAGES * SB);
+    uint64_t *conv = full + C::STAGES;
+    uint64_t *empty = conv + C::STAGES;
+    uint64_t *accf = empty + C::STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accf + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tile = blockIdx.x / npass;
+    const int pass = (int)(blockIdx.x % npass);
+    const int64_t row0 = tile * kBM;
+    const int col0 = pass * kNP;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], 4);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmx) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmb0) : "memory");
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % C::STAGES;
+                const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 1)) break;
+                uint8_t *st = smem + s * SB;
+                mbar_expect_tx(&full[s], (uint32_t)(C::XBOX + C::NA) * kTile);
+#pragma unroll
+                for (int b = 0; b < C::XBOX; ++b)
+                    tma_load_2d(st + b * kTile, &tmx, kb * C::BK + b * 32, (int)row0, &full[s]);
+                uint8_t *bs = st + (C::XBOX + C::NA) * kTile;
+                tma_load_2d(bs, &tmb0, kb * C::BK, col0, &full[s]);
+                if (C::NA == 2) tma_load_2d(bs + kTile, &tmb1, kb * C::BK, col0, &full[s]);
+                issued = kb + 1;
+            }
+            // drain: the last loads of each stage must land before the CTA exits
+            for (int kb = std::max(0, issued - C::STAGES); kb < issued; ++kb) {
+                const int s = kb % C::STAGES;
+                const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try(&full[s], ph) && globaltimer() - t0 < kWaitNs) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc<MODE>();
+            constexpr int KSTEPS = 4;  // 32-byte K steps per 128-byte row
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % C::STAGES;
+                const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+                if (!mbar_wait(&conv[s], ph, abort_flag, err, 2)) break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * SB);
+                const uint64_t a0 = umma_desc(st + C::XBOX * kTile);
+                const uint64_t a1 = umma_desc(st + (C::XBOX + 1) * kTile);
+                const uint64_t b0 = umma_desc(st + (C::XBOX + C::NA) * kTile);
+                const uint64_t b1 = umma_desc(st + (C::XBOX + C::NA + 1) * kTile);
+#pragma unroll
+                for (int kk = 0; kk < KSTEPS; ++kk) {
+                    const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
+                    umma<MODE>(tmem, a0 + off, b0 + off, idesc, (kb | kk) != 0);
+                    if (C::NA == 2) {
+                        umma<MODE>(tmem, a0 + off, b1 + off, idesc, 1u);
+                        umma<MODE>(tmem, a1 + off, b0 + off, idesc, 1u);
+                    }
+                }
+                umma_commit(&empty[s]);
+            }
+            umma_commit(accf);
+        }
+        __syncwarp();
+    } else {
+        // ---- converters (one tile row per thread)
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const bool row_ok = row0 + r < n;
+        float nrm = 0.f;
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int s = kb % C::STAGES;
+            const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+            int got = 0;
+            if (lane == 0) got = mbar_wait(&full[s], ph, abort_flag, err, 3) ? 1 : 0;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) { ok = false; break; }
+            uint8_t *st = smem + s * SB;
+            uint8_t *a0 = st + C::XBOX * kTile;
+            const float *mk = mean_pad + (size_t)kb * C::BK;
+            if (MODE == kFP8) {
+                // 8 chunks of 16 E4M3 values = 4 staging chunks of 4 FP32 each
+#pragma unroll
+                for (int ac = 0; ac < 8; ++ac) {
+                    const uint8_t *xb = st + (ac >> 1) * kTile;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int c = (ac & 1) * 4 + h;
+                        const float4 x = *reinterpret_cast<const float4 *>(xb + swz(r, c));
+                        const float4 m = *reinterpret_cast<const float4 *>(mk + ac * 16 + h * 4);
+                        const float y0 = x.x - m.x, y1 = x.y - m.y, y2 = x.z - m.z, y3 = x.w - m.w;
+                        nrm = fmaf(y0, y0, nrm); nrm = fmaf(y1, y1, nrm);
+                        nrm = fmaf(y2, y2, nrm); nrm = fmaf(y3, y3, nrm);
+                        const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+                            make_float2(y0 * x_scale, y1 * x_scale), __NV_SATFINITE, __NV_E4M3);
+                        const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                            make_float2(y2 * x_scale, y3 * x_scale), __NV_SATFINITE, __NV_E4M3);
+                        w[h] = (uint32_t)lo | ((uint32_t)hi << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(a0 + swz(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            } else {
+                uint8_t *a1 = a0 + kTile;
+#pragma unroll
+                for (int ac = 0; ac < 8; ++ac) {
+                    const uint8_t *xb = st + (ac >> 2) * kTile;
+                    const int c0 = (ac & 3) * 2;
+                    const float4 x0 = *reinterpret_cast<const float4 *>(xb + swz(r, c0));
+                    const float4 x1 = *reinterpret_cast<const float4 *>(xb + swz(r, c0 + 1));
+                    const float4 m0 = *reinterpret_cast<const float4 *>(mk + ac * 8);
+                    const float4 m1 = *reinterpret_cast<const float4 *>(mk + ac * 8 + 4);
+                    float y[8] = {x0.x - m0.x, x0.y - m0.y, x0.z - m0.z, x0.w - m0.w,
+                                  x1.x - m1.x, x1.y - m1.y, x1.z - m1.z, x1.w - m1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) nrm = fmaf(y[i], y[i], nrm);
+                    if (MODE == kBF16) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            w[i] = pack_b2(__floats2bfloat162_rn(y[2 * i], y[2 * i + 1]));
+                        *reinterpret_cast<uint4 *>(a0 + swz(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+                        uint32_t wh[4], wl[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float s0 = y[2 * i] * x_scale, s1 = y[2 * i + 1] * x_scale;
+                            const __half2 h = __floats2half2_rn(s0, s1);
+                            const float2 hf = __half22float2(h);
+                            wh[i] = pack_h2(h);
+                            wl[i] = pack_h2(__floats2half2_rn(s0 - hf.x, s1 - hf.y));
+                        }
+                        *reinterpret_cast<uint4 *>(a0 + swz(r, ac)) =
+                            make_uint4(wh[0], wh[1], wh[2], wh[3]);
+                        *reinterpret_cast<uint4 *>(a1 + swz(r, ac)) =
+                            make_uint4(wl[0], wl[1], wl[2], wl[3]);
+                    }
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[s]);
+        }
+        // ---- epilogue: accumulator row r -> O
+        int ready = 0;
+        if (ok && lane == 0) ready = mbar_wait(accf, 0, abort_flag, err, 4) ? 1 : 0;
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (ready) {
+            tc_fence_after();
+            float *orow = O + (row0 + r) * ldo;
+            const bool vec = ((ldo & 3) == 0) && ((((uintptr_t)O) & 15) == 0);
+#pragma unroll 1
+            for (int c = 0; c < kNP; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                const int col = col0 + c;
+                if (!row_ok || col >= dk) continue;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] *= col_scale[col + i];
+                if (vec && col + 16 <= dk) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4 *>(orow + col + i) =
+                            make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                } else {
+                    for (int i = 0; i < 16 && col + i < dk; ++i) orow[col + i] = v[i];
+                }
+            }
+        }
+        if (pass == 0 && row_ok && norms) norms[(row0 + r) * nstride] = nrm;
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        // the accumulator may still be written by MMAs issued before an abort
+        if (lane == 0 && *abort_flag) {
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try(accf, 0) && globaltimer() - t0 < kWaitNs) {
+            }
+        }
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+saq_status get_encoder(PFN_cuTensorMapEncodeTiled_v12000 *fn) {
+    std::call_once(g_encode_once, []() {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    if (!g_encode) return set_error(SAQ_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    *fn = g_encode;
+    return SAQ_OK;
+}
+
+saq_status make_map(CUtensorMap *map, CUtensorMapDataType type, int elem, const void *ptr,
+                    uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc;
+    saq_status st = get_encoder(&enc);
+    if (st != SAQ_OK) return st;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * (uint64_t)elem};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(map, type, 2, const_cast<void *>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(SAQ_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return SAQ_OK;
+}
+
+struct TcExtra {
+    CUtensorMap b0, b1;
+    float *mean_pad = nullptr;
+    float x_scale = 1.f;
+    int *err = nullptr;
+};
+
+double pow2_near(double x) { return ldexp(1.0, (int)lround(log2(x))); }
+
+template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, int64_t n,
+                                           float *O, int64_t ldo, float *norms, int64_t ns,
+                                           cudaStream_t s) {
+    const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
+    CUtensorMap tmx;
+    saq_status st = make_map(&tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, (uint64_t)m->d,
+                             (uint64_t)n, 32, kBM);
+    if (st != SAQ_OK) return st;
+    const int npass = (m->dk + kNP - 1) / kNP;
+    const int nkb = (m->d + Cfg<MODE>::BK - 1) / Cfg<MODE>::BK;
+    SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_bytes<MODE>()));
+    const int64_t tiles = (n + kBM - 1) / kBM;
+    const int64_t blocks = tiles * npass;
+    if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
+    k_proj_tc<MODE><<<(unsigned)blocks, kThreads, smem_bytes<MODE>(), s>>>(
+        tmx, ex->b0, ex->b1, n, m->dk, npass, nkb, ex->mean_pad, ex->x_scale, m->tc.col_scale, O,
+        ldo, norms, ns, ex->err);
+    note_launches();
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return SAQ_OK;
+}
+
+}  // namespace
+
+bool tc_supported(const saq_model *m) { return m->d % 4 == 0 && m->dk > 0; }
+
+void tc_release(saq_model *m) {
+    TcExtra *ex = static_cast<TcExtra *>(m->tc.extra);
+    if (ex) {
+        cudaFree(ex->mean_pad);
+        cudaFree(ex->err);
+        delete ex;
+    }
+    cudaFree(m->tc.w_hi);
+    cudaFree(m->tc.w_lo);
+    cudaFree(m->tc.col_scale);
+    m->tc = TcOperands{};
+}
+
+// Device operands of W for `precision`: zero-padded to dk_pad x d_pad, plus
+// the per-column dequantisation scale and the padded mean.
+saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
+    if (!tc_supported(m))
+        return set_error(SAQ_ERR_UNSUPPORTED, "tensor-core projection needs d %% 4 == 0");
+    tc_release(m);
+    const int BK = precision == SAQ_PREC_FP8 ? 128 : 64;
+    const int dpad = (m->d + BK - 1) / BK * BK;
+    const int dkpad = (m->dk + kNP - 1) / kNP * kNP;
+    const int d = m->d, dk = m->dk;
+    // input scale from the fitted variances (a power of two: exact)
+    double tot = 0;
+    for (double v : m->sig2) tot += v;
+    const double rms = tot > 0 ? sqrt(tot / d) : 0.0;
+    double xs = 1.0, ws = 1.0;
+    std::vector<float> cs((size_t)dkpad, 0.f);
+    TcExtra *ex = new TcExtra();
+    m->tc.extra = ex;
+    m->tc.precision = precision;
+    m->tc.dk_pad = dkpad;
+    m->tc.d_pad = dpad;
+    if (precision == SAQ_PREC_FP32) {
+        xs = rms > 0 ? pow2_near(8.0 / rms) : 1.0;
+        ws = 1024.0;
+        std::vector<__half> hi((size_t)dkpad * dpad, __float2half(0.f)), lo = hi;
+        for (int i = 0; i < dk; ++i)
+            for (int k = 0; k < d; ++k) {
+                const double w = m->W[(size_t)i * d + k] * ws;
+                const __half h = __double2half(w);
+                hi[(size_t)i * dpad + k] = h;
+                lo[(size_t)i * dpad + k] = __double2half(w - (double)__half2float(h));
+            }
+        SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_hi, hi.size() * 2));
+        SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_lo, lo.size() * 2));
+        SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice));
+        SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice));
+        for (int i = 0; i < dk; ++i) cs[(size_t)i] = (float)(1.0 / (xs * ws));
+    } else if (precision == SAQ_PREC_BF16) {
+        std::vector<__nv_bfloat16> b((size_t)dkpad * dpad, __float2bfloat16(0.f));
+        for (int i = 0; i < dk; ++i)
+            for (int k = 0; k < d; ++k)
+                b[(size_t)i * dpad + k] = __float2bfloat16((float)m->W[(size_t)i * d + k]);
+        SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_hi, b.size() * 2));
+        SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_hi, b.data(), b.size() * 2, cudaMemcpyHostToDevice));
+        for (int i = 0; i < dk; ++i) cs[(size_t)i] = 1.f;
+    } else if (precision == SAQ_PREC_FP8) {
+        // E4M3: inputs scaled so the per-coordinate rms maps to 16 (max 448),
+        // each kept segment's rows scaled by a power of two so |w| <= 448.
+        xs = rms > 0 ? pow2_near(16.0 / rms) : 1.0;
+        std::vector<uint8_t> b((size_t)dkpad * dpad, 0);
+        for (const KeptSeg &k : m->kept) {
+            double amax = 0;
+            for (int i = k.off; i < k.off + k.len; ++i)
+                for (int j = 0; j < d; ++j) amax = std::max(amax, fabs(m->W[(size_t)i * d + j]));
+            const double sb = amax > 0 ? ldexp(1.0, (int)floor(log2(448.0 / amax))) : 1.0;
+            for (int i = k.off; i < k.off + k.len; ++i) {
+                for (int j = 0; j < d; ++j)
+                    b[(size_t)i * dpad + j] = (uint8_t)__nv_cvt_double_to_fp8(
+                        m->W[(size_t)i * d + j] * sb, __NV_SATFINITE, __NV_E4M3);
+                cs[(size_t)i] = (float)(1.0 / (xs * sb));
+            }
+        }
+        SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_hi, b.size()));
+        SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_hi, b.data(), b.size(), cudaMemcpyHostToDevice));
+    } else {
+        return set_error(SAQ_ERR_INVALID, "precision %d has no tensor-core form", precision);
+    }
+    ex->x_scale = (float)xs;
+    SAQ_CUDA_CHECK(cudaMalloc(&m->tc.col_scale, sizeof(float) * cs.size()));
+    SAQ_CUDA_CHECK(cudaMemcpy(m->tc.col_scale, cs.data(), sizeof(float) * cs.size(),
+                              cudaMemcpyHostToDevice));
+    std::vector<float> mp((size_t)dpad, 0.f);
+    for (int k = 0; k < d; ++k) mp[(size_t)k] = (float)m->mean[(size_t)k];
+    SAQ_CUDA_CHECK(cudaMalloc(&ex->mean_pad, sizeof(float) * mp.size()));
+    SAQ_CUDA_CHECK(cudaMemcpy(ex->mean_pad, mp.data(), sizeof(float) * mp.size(),
+                              cudaMemcpyHostToDevice));
+    SAQ_CUDA_CHECK(cudaMalloc(&ex->err, sizeof(int)));
+    SAQ_CUDA_CHECK(cudaMemset(ex->err, 0, sizeof(int)));
+    const bool f8 = precision == SAQ_PREC_FP8;
+    const CUtensorMapDataType t = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                     : (precision == SAQ_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const int es = f8 ? 1 : 2;
+    saq_status st = make_map(&ex->b0, t, es, m->tc.w_hi, (uint64_t)dpad, (uint64_t)dkpad,
+                             (uint32_t)BK, kNP);
+    if (st != SAQ_OK) return st;
+    ex->b1 = ex->b0;
+    if (m->tc.w_lo) {
+        st = make_map(&ex->b1, t, es, m->tc.w_lo, (uint64_t)dpad, (uint64_t)dkpad, (uint32_t)BK,
+                      kNP);
+        if (st != SAQ_OK) return st;
+    }
+    return SAQ_OK;
+}
+
+saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, float *O,
+                             int64_t ldo, float *norms2, int64_t norms_stride, cudaStream_t s) {
+    if (n <= 0) return SAQ_OK;
+    if (((uintptr_t)X & 15u) != 0) return set_error(SAQ_ERR_INVALID, "X not 16-byte aligned");
+    switch (m->tc.precision) {
+        case SAQ_PREC_FP32: return launch_mode<kSplit>(m, X, n, O, ldo, norms2, norms_stride, s);
+        case SAQ_PREC_BF16: return launch_mode<kBF16>(m, X, n, O, ldo, norms2, norms_stride, s);
+        case SAQ_PREC_FP8: return launch_mode<kFP8>(m, X, n, O, ldo, norms2, norms_stride, s);
+    }
+    return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
+}
+
+saq_status tc_check_error(const saq_model *m, cudaStream_t s) {
+    const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
+    if (!ex || !ex->err) return SAQ_OK;
+    int h = 0;
+    SAQ_CUDA_CHECK(cudaMemcpyAsync(&h, ex->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SAQ_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (h != 0) {
+        cudaMemsetAsync(ex->err, 0, sizeof(int), s);
+        return set_error(SAQ_ERR_TIMEOUT, "tensor-core projection: a device wait timed out (role %d)", h);
+    }
+    return SAQ_OK;
 }
 
 }  // namespace saq

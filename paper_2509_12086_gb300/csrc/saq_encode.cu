@@ -215,6 +215,17 @@ saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
     return SAQ_OK;
 }
 
+int32_t saq_model_uses_tensor_cores(const saq_model *m) { return (m && use_tc(m)) ? 1 : 0; }
+
+saq_status saq_check_device(const saq_model *m, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    SAQ_CUDA_CHECK(cudaStreamSynchronize(s));
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return tc_check_error(m, s);
+}
+
 saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
                              const float *factors_dev, int64_t n, const float *Q_dev, int64_t nq,
                              int32_t prefix_bits, float *dist_dev, void *stream) {

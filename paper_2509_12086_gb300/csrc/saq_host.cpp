@@ -167,12 +167,9 @@ void model_release_device(saq_model *m) {
     if (!m) return;
     cudaFree(m->d_mean);
     cudaFree(m->d_W);
-    cudaFree(m->tc.w_hi);
-    cudaFree(m->tc.w_lo);
-    cudaFree(m->tc.col_scale);
+    tc_release(m);
     m->d_mean = nullptr;
     m->d_W = nullptr;
-    m->tc = TcOperands{};
 }
 
 saq_status model_finalize(saq_model *m) {

@@ -47,6 +47,7 @@ struct TcOperands {
     float *col_scale = nullptr;  // per output column dequant scale (dk_pad)
     int dk_pad = 0;
     int d_pad = 0;
+    void *extra = nullptr;    // tensor maps, padded mean, error word (k_tc.cu)
 };
 
 }  // namespace saq
@@ -94,6 +95,10 @@ saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n,
                              float *O, int64_t ldo, float *norms2,
                              int64_t norms_stride, cudaStream_t s);
 bool tc_supported(const saq_model *m);
+void tc_release(saq_model *m);
+// Reads and clears the device error word of the tensor-core projection
+// (synchronises `s`); SAQ_ERR_TIMEOUT if a bounded wait gave up.
+saq_status tc_check_error(const saq_model *m, cudaStream_t s);
 // norms2[i * stride] = |x_i - c|^2
 saq_status launch_rownorm2(const saq_model *m, const float *X, int64_t n,
                            float *out, int64_t stride, cudaStream_t s);

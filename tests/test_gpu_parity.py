@@ -243,3 +243,60 @@ def test_c2_full_size_sampled_rows():
     dg = m.estimate_dist(codes[torch.from_numpy(sub).cuda()], factors[torch.from_numpy(sub).cuda()],
                          torch.from_numpy(Qm).cuda()).cpu().numpy().astype(np.float64)
     assert abs(O.relative_error(dg, ex).mean() - O.relative_error(do, ex).mean()) <= DIST_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32_simt", 5e-6), ("fp32", 5e-6), ("bf16", 5e-3),
+                                      ("fp8", 5e-2)])
+def test_projection_accuracy(c1, prec, tol):
+    """saq_project against the oracle's FP64 projection, error relative to the
+    row norm |x - c|: FP32 (CUDA cores, or the FP16-split tensor-core GEMM) at
+    FP32 rounding level, BF16 and FP8 at their operand rounding."""
+    X, Qm, mo, eo = c1
+    m = lib_model(mo, prec)
+    assert m.tensor_cores == (prec != "fp32_simt")
+    Ol, n2 = m.project(torch.from_numpy(X).cuda())
+    m.check_device()
+    Oo, n2o = O.project(X, mo)
+    rel = np.abs(Ol.cpu().numpy().astype(np.float64) - Oo) / np.sqrt(n2o)[:, None]
+    assert rel.max() <= tol, rel.max()
+    assert np.allclose(n2.cpu().numpy(), n2o, rtol=1e-5)
+
+
+@pytest.mark.parametrize("n,d,plan", [
+    (1, 128, [(0, 64, 5), (64, 64, 3)]),
+    (300, 200, [(0, 64, 8), (64, 72, 3), (136, 32, 1), (168, 32, 0)]),
+    (1000, 960, [(0, 64, 8), (64, 192, 5), (256, 256, 4), (512, 448, 3)]),
+])
+def test_tensor_core_projection_ragged(n, d, plan):
+    """Ragged rows (not a multiple of the 128-row tile), ragged K (d = 200 is
+    not a multiple of the 64-wide K block) and ragged columns (d_kept = 168)."""
+    mo = _random_model(d, plan, seed=d)
+    rng = np.random.default_rng(n)
+    X = (rng.standard_normal((n, d)) * np.linspace(1, 0.05, d)).astype(np.float32)
+    m = lib_model(mo, "fp32")
+    assert m.tensor_cores
+    Ol, n2 = m.project(torch.from_numpy(X).cuda())
+    m.check_device()
+    Oo, n2o = O.project(X, mo)
+    rel = np.abs(Ol.cpu().numpy().astype(np.float64) - Oo) / np.sqrt(n2o)[:, None]
+    assert rel.max() <= 5e-6
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_precision_forms_error_bounded(c1, prec):
+    """BF16 / FP8 projection (quantization and adjustment stay FP32): codes
+    differ from the oracle's where the projection error crosses a decision,
+    so only the error statistics are bounded: mean quantization error within
+    10% (BF16) / 50% (FP8) of the oracle's, estimator error within 2x."""
+    X, Qm, mo, eo = c1
+    m = lib_model(mo, prec)
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    f = factors.cpu().numpy().astype(np.float64)
+    eg, eo_ = O.quant_error(f, mo).mean(), O.quant_error(eo.factors, mo).mean()
+    lim = 0.10 if prec == "bf16" else 0.50
+    assert abs(eg - eo_) <= lim * eo_, (eg, eo_)
+    dg = m.estimate_dist(codes, factors, torch.from_numpy(Qm).cuda()).cpu().numpy()
+    ex = O.exact_dist(X, Qm)
+    rg = O.relative_error(dg.astype(np.float64), ex).mean()
+    ro = O.relative_error(O.estimate(mo, eo.codes, eo.factors, Qm), ex).mean()
+    assert rg <= 2.0 * ro + 1e-4, (rg, ro)
