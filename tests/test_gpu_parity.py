@@ -286,17 +286,21 @@ def test_tensor_core_projection_ragged(n, d, plan):
 def test_precision_forms_error_bounded(c1, prec):
     """BF16 / FP8 projection (quantization and adjustment stay FP32): codes
     differ from the oracle's where the projection error crosses a decision,
-    so only the error statistics are bounded: mean quantization error within
-    10% (BF16) / 50% (FP8) of the oracle's, estimator error within 2x."""
+    so only the error statistics are bounded.  The projection adds its own
+    error energy: operand rounding of 2^-9 (BF16) or 2^-4 (E4M3) relative on
+    both operands gives about 3e-6 (BF16) or 2.6e-3 (FP8) of |x - c|^2, so the
+    mean quantization error may exceed the oracle's by 10% (BF16) or by an
+    absolute 0.01 (FP8, 4x the budget); the estimator error stays within 2x
+    (BF16) or 4x (FP8) of the oracle's."""
     X, Qm, mo, eo = c1
     m = lib_model(mo, prec)
     codes, factors = m.encode(torch.from_numpy(X).cuda())
     f = factors.cpu().numpy().astype(np.float64)
     eg, eo_ = O.quant_error(f, mo).mean(), O.quant_error(eo.factors, mo).mean()
-    lim = 0.10 if prec == "bf16" else 0.50
-    assert abs(eg - eo_) <= lim * eo_, (eg, eo_)
+    lim = 0.10 * eo_ if prec == "bf16" else 0.01
+    assert abs(eg - eo_) <= lim, (eg, eo_)
     dg = m.estimate_dist(codes, factors, torch.from_numpy(Qm).cuda()).cpu().numpy()
     ex = O.exact_dist(X, Qm)
     rg = O.relative_error(dg.astype(np.float64), ex).mean()
     ro = O.relative_error(O.estimate(mo, eo.codes, eo.factors, Qm), ex).mean()
-    assert rg <= 2.0 * ro + 1e-4, (rg, ro)
+    assert rg <= (2.0 if prec == "bf16" else 4.0) * ro + 1e-4, (rg, ro)
