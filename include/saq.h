@@ -252,6 +252,58 @@ int32_t saq_model_uses_tensor_cores(const saq_model *m);
  * cleared).  Failure detection for the asynchronous entry points. */
 saq_status saq_check_device(const saq_model *m, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous-batching ingest over several resident collections.
+ * (The paper's encoder is offline; this runtime applies saq_encode to a
+ * stream of insert requests.)
+ *
+ * Each collection is a fitted model kept resident on the device.  Requests
+ * (host rows of one collection) queue on submit; a scheduler thread packs
+ * queued requests of one collection, oldest first, into batches of at most
+ * max_batch_rows rows (large requests are split across batches) and runs each
+ * batch on one of `slots` streams: copy-in, the encode kernels, copy-out.  A
+ * request that arrives while others are on the GPU joins the next batch of its
+ * collection as soon as a slot is free, so batches of different collections
+ * and the copies of one batch overlap the encode of another.  Admission is by
+ * HBM budget: slot buffers (inputs, codes, factors, projection scratch) are
+ * allocated once at open, and open fails with SAQ_ERR_OOM if `slots` slots do
+ * not fit in hbm_budget_bytes.  Results are identical to saq_encode on the
+ * same rows: every row is encoded independently.
+ * ------------------------------------------------------------------------ */
+typedef struct saq_ingest saq_ingest;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory the service may hold       */
+    int32_t max_batch_rows;   /* rows per batch launch (>= 1)              */
+    int32_t slots;            /* concurrent batches (streams), >= 1        */
+} saq_ingest_params;
+
+typedef struct {
+    uint64_t submitted, completed, rows_completed, batches;
+    double p50_latency_s, p99_latency_s, max_latency_s;  /* submit -> done */
+    double busy_s;            /* wall time between first submit and last completion */
+} saq_ingest_stats;
+
+/* models[n_models] stay owned by the caller and must outlive the service. */
+saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
+                           const saq_ingest_params *p, saq_ingest **out);
+/* Queue n rows (host, row-major n x d of the collection's model) whose codes
+ * and factors go to codes_host / factors_host (sized as for saq_encode).
+ * Page-locked host memory is recommended.  Buffers must stay valid until the
+ * request completes.  Never blocks on the GPU; *ticket identifies it. */
+saq_status saq_ingest_submit(saq_ingest *s, int32_t collection, const float *X_host,
+                             int64_t n, uint8_t *codes_host, float *factors_host,
+                             uint64_t *ticket);
+/* *done = 1 once the request's outputs are in host memory. */
+saq_status saq_ingest_poll(saq_ingest *s, uint64_t ticket, int32_t *done);
+/* Wait up to timeout_ms (< 0: no limit) for the request; SAQ_ERR_TIMEOUT if
+ * it is still in flight.  *latency_s (may be NULL) receives submit-to-done. */
+saq_status saq_ingest_wait(saq_ingest *s, uint64_t ticket, int32_t timeout_ms,
+                           double *latency_s);
+saq_status saq_ingest_get_stats(saq_ingest *s, saq_ingest_stats *out);
+/* Waits for all queued and in-flight requests, then frees the service. */
+saq_status saq_ingest_close(saq_ingest *s);
+
 /* Number of CUDA kernels the library has launched in this process so far
  * (all threads, all devices).  Diagnostic; never reset. */
 uint64_t saq_kernel_launch_count(void);

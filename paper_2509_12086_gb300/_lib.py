@@ -34,7 +34,21 @@ EXPORTS = [
     "saq_estimate_dist", "saq_model_export", "saq_model_import", "saq_last_error",
     "saq_status_string", "saq_plan_search", "saq_kernel_launch_count",
     "saq_encode_noalloc", "saq_model_uses_tensor_cores", "saq_check_device",
+    "saq_ingest_open", "saq_ingest_submit", "saq_ingest_poll", "saq_ingest_wait",
+    "saq_ingest_get_stats", "saq_ingest_close",
 ]
+
+
+class saq_ingest_params(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_rows", ctypes.c_int32),
+                ("slots", ctypes.c_int32)]
+
+
+class saq_ingest_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rows_completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+                ("max_latency_s", ctypes.c_double), ("busy_s", ctypes.c_double)]
 
 
 class saq_params(ctypes.Structure):
@@ -96,6 +110,13 @@ def load() -> ctypes.CDLL:
         "saq_encode_noalloc": (st, [mp, vp, i64, vp, vp, vp]),
         "saq_model_uses_tensor_cores": (i32, [mp]),
         "saq_check_device": (st, [mp, vp]),
+        "saq_ingest_open": (st, [ctypes.POINTER(mp), i32, ctypes.POINTER(saq_ingest_params),
+                                 ctypes.POINTER(vp)]),
+        "saq_ingest_submit": (st, [vp, i32, vp, i64, vp, vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "saq_ingest_poll": (st, [vp, ctypes.c_uint64, ctypes.POINTER(i32)]),
+        "saq_ingest_wait": (st, [vp, ctypes.c_uint64, i32, ctypes.POINTER(ctypes.c_double)]),
+        "saq_ingest_get_stats": (st, [vp, ctypes.POINTER(saq_ingest_stats)]),
+        "saq_ingest_close": (st, [vp]),
         "saq_plan_search": (st, [dp, i32, i32, i64, i32, ctypes.c_double,
                                  ctypes.POINTER(saq_segment), i32, ctypes.POINTER(i32), dp]),
     }
@@ -331,3 +352,61 @@ def saq_encode(model: Model, X, codes=None, factors=None, stream=None):
 
 def saq_estimate_dist(model: Model, codes, factors, Q, prefix_bits=0, stream=None):
     return model.estimate_dist(codes, factors, Q, prefix_bits, stream)
+
+
+class Ingest:
+    """Continuous-batching ingest service over resident collections
+    (saq_ingest_* in include/saq.h).  Host buffers passed to submit must stay
+    alive until the request completes; this wrapper keeps references."""
+
+    def __init__(self, models: Sequence[Model], hbm_budget_bytes: int, max_batch_rows: int = 65536,
+                 slots: int = 4):
+        self._models = list(models)
+        arr = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
+        p = saq_ingest_params(hbm_budget_bytes, max_batch_rows, slots)
+        h = ctypes.c_void_p()
+        _check(load().saq_ingest_open(arr, len(models), ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, collection: int, X: torch.Tensor, codes: torch.Tensor = None,
+               factors: torch.Tensor = None) -> int:
+        assert (not X.is_cuda) and X.dtype == torch.float32 and X.is_contiguous()
+        m = self._models[collection]
+        n = X.shape[0]
+        if codes is None:
+            codes = torch.empty((n, max(m.code_bytes, 1)), dtype=torch.uint8)
+            factors = torch.empty((n, m.factor_count), dtype=torch.float32)
+        t = ctypes.c_uint64()
+        _check(load().saq_ingest_submit(self._h, collection, ctypes.c_void_p(X.data_ptr()), n,
+                                        ctypes.c_void_p(codes.data_ptr()),
+                                        ctypes.c_void_p(factors.data_ptr()), ctypes.byref(t)))
+        self._keep[t.value] = (X, codes, factors, m.code_bytes)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        lat = ctypes.c_double()
+        _check(load().saq_ingest_wait(self._h, ticket, timeout_ms, ctypes.byref(lat)))
+        X, codes, factors, cb = self._keep.pop(ticket)
+        return codes[:, :cb], factors, lat.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        _check(load().saq_ingest_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def stats(self) -> dict:
+        s = saq_ingest_stats()
+        _check(load().saq_ingest_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in saq_ingest_stats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(load().saq_ingest_close(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

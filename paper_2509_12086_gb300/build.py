@@ -17,7 +17,7 @@ OUT = os.path.join(HERE, "libsaq.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["saq_host.cpp", "saq_encode.cu", "k_simt.cu", "k_caq.cu", "k_estimate.cu",
-           "k_fit.cu", "k_tc.cu", "saq_noalloc.cu"]
+           "k_fit.cu", "k_tc.cu", "saq_noalloc.cu", "saq_ingest.cu"]
 
 
 def _nvcc():
@@ -65,7 +65,7 @@ def build(verbose=False):
     if (not os.path.exists(OUT)
             or any(os.path.getmtime(o) > os.path.getmtime(OUT) for o in objs)):
         cmd = [_nvcc()] + ARCH + ["-shared", "-o", OUT + ".tmp"] + objs + [
-            "-lcusolver", "-lcublas", "-lcudart",
+            "-lcusolver", "-lcublas", "-lcudart", "-lpthread",
             "-Xlinker", "-rpath=" + os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")]
         subprocess.check_call(cmd)
         os.replace(OUT + ".tmp", OUT)

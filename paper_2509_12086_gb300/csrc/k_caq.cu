@@ -22,7 +22,11 @@
 // (square both sides of I'/sqrt(S') > I/sqrt(S); the moves that could make
 // I' <= 0 are never improving).  Both sides are first-order quantities, so
 // FP32 decides correctly down to relative cosine margins far below 1e-7.
-// I is recomputed exactly at the start of every round.
+// I and S are recomputed exactly at the start of every round; within a
+// round the eligible lanes of a chunk are a uniform bit mask ANDed into the
+// ballot, and the two thresholds of the current chunk (u+1, 1-u, or +inf at
+// the edge of the grid) are kept in registers, so a pass without a move costs
+// a handful of instructions and each accepted move one shuffle-and-update.
 #include "saq_internal.h"
 
 namespace saq {
@@ -46,7 +50,7 @@ __device__ __forceinline__ float warp_max(float x) {
 }
 
 template <int NCH>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (NCH >= 24) ? 1 : 2)
 k_caq(const float *__restrict__ O, int64_t ldo, int64_t n, int col, int len, int B,
       int rounds, uint8_t *__restrict__ codes, int64_t code_stride, int64_t code_off,
       int words, float *__restrict__ factors, int nf, int fidx) {
@@ -99,45 +103,65 @@ k_caq(const float *__restrict__ O, int64_t ldo, int64_t n, int col, int len, int
     S = warp_sum_i(S);
     float Sf = (float)S;
 
+    const float kInf = __int_as_float(0x7f800000);
     for (int r = 0; r < rounds; ++r) {
+        // exact state at the start of the round
         float I = 0.f;
+        int Si = 0;
 #pragma unroll
-        for (int m = 0; m < NCH; ++m) I = fmaf(u[m], o[m], I);
+        for (int m = 0; m < NCH; ++m) {
+            I = fmaf(u[m], o[m], I);
+            Si += (int)u[m] * (int)u[m];
+        }
         I = warp_sum(I);
-        float alpha = __fdividef(Sf, I);
-        float beta = __fdividef(alpha, I);
+        Sf = (float)warp_sum_i(Si);
+        float rI = __fdividef(1.f, I);
+        float alpha = Sf * rI;
+        float beta = alpha * rI;
         bool moved = false;
 #pragma unroll
         for (int m = 0; m < NCH; ++m) {
             if (m * 32 >= len) break;
-            const bool inside = (m * 32 + lane) < len;
-            int start = -1;
+            const float om = o[m];
+            const float o2 = om * om;
+            // thresholds of the two moves; +inf where the move leaves the grid
+            // (padding lanes have o = u = 0 and never pass them)
+            float up1 = u[m] < cmaxf ? u[m] + 1.f : kInf;
+            float um1 = u[m] > -cmaxf ? 1.f - u[m] : kInf;
+            unsigned eligible = 0xffffffffu;
             while (true) {
-                const float om = o[m], um = u[m];
-                const float t = om * om * beta;
-                const float dp = fmaf(om, alpha, t) - um;
-                const float dm = fmaf(-om, alpha, t) + um;
-                const bool ap = (dp > 1.f) && (um < cmaxf);
-                const bool am = (dm > 1.f) && (um > -cmaxf);
-                const bool acc = (ap || am) && inside && (lane > start);
-                const unsigned mask = __ballot_sync(0xffffffffu, acc);
+                const float t = o2 * beta;
+                const bool ap = fmaf(om, alpha, t) > up1;
+                const bool am = fmaf(-om, alpha, t) > um1;
+                const unsigned mask = __ballot_sync(0xffffffffu, ap || am) & eligible;
                 if (mask == 0u) break;
                 const int p = __ffs(mask) - 1;
-                const unsigned pm = __ballot_sync(0xffffffffu, ap);
-                const float sgn = ((pm >> p) & 1u) ? 1.f : -1.f;
+                const bool plus = (__ballot_sync(0xffffffffu, ap) >> p) & 1u;
+                const float sgn = plus ? 1.f : -1.f;
                 const float op = __shfl_sync(0xffffffffu, om, p);
-                const float up = __shfl_sync(0xffffffffu, um, p);
+                const float up = __shfl_sync(0xffffffffu, u[m], p);
                 I = fmaf(2.f * sgn, op, I);
-                S += 4 * (int)(sgn * up) + 4;
-                Sf = (float)S;
-                alpha = __fdividef(Sf, I);
-                beta = __fdividef(alpha, I);
-                if (lane == p) u[m] = um + 2.f * sgn;
-                start = p;
+                Sf += fmaf(4.f * sgn, up, 4.f);
+                rI = __fdividef(1.f, I);
+                alpha = Sf * rI;
+                beta = alpha * rI;
+                if (lane == p) {
+                    const float un = up + 2.f * sgn;
+                    u[m] = un;
+                    up1 = un < cmaxf ? un + 1.f : kInf;
+                    um1 = un > -cmaxf ? 1.f - un : kInf;
+                }
+                eligible = (p == 31) ? 0u : (0xfffffffeu << p);
                 moved = true;
             }
         }
         if (!moved) break;  // a round without a move leaves the state unchanged
+    }
+    {
+        int Si = 0;
+#pragma unroll
+        for (int m = 0; m < NCH; ++m) Si += (int)u[m] * (int)u[m];
+        Sf = (float)warp_sum_i(Si);
     }
 
     float I = 0.f;

@@ -114,6 +114,9 @@ saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O,
                         float *norms, int64_t nstride, cudaStream_t s);
 saq_status quantize_rows(const saq_model *m, const float *O, int64_t ldo, int64_t n,
                          uint8_t *codes, float *factors, cudaStream_t s);
+// The whole encode of rows [0, n) with O scratch of `rows` rows (saq_encode.cu).
+saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
+                       float *factors, float *O, int64_t rows, cudaStream_t s);
 // Estimator.
 saq_status launch_estimate(const saq_model *m, const uint8_t *codes,
                            const float *factors, int64_t n, const float *Qrot,
