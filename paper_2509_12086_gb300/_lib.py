@@ -372,16 +372,18 @@ class Ingest:
     def submit(self, collection: int, X: torch.Tensor, codes: torch.Tensor = None,
                factors: torch.Tensor = None) -> int:
         assert (not X.is_cuda) and X.dtype == torch.float32 and X.is_contiguous()
-        m = self._models[collection]
         n = X.shape[0]
+        # an out-of-range collection is rejected by the library itself
+        m = self._models[collection] if 0 <= collection < len(self._models) else None
+        cb = m.code_bytes if m is not None else 1
         if codes is None:
-            codes = torch.empty((n, max(m.code_bytes, 1)), dtype=torch.uint8)
-            factors = torch.empty((n, m.factor_count), dtype=torch.float32)
+            codes = torch.empty((n, max(cb, 1)), dtype=torch.uint8)
+            factors = torch.empty((n, m.factor_count if m is not None else 1), dtype=torch.float32)
         t = ctypes.c_uint64()
         _check(load().saq_ingest_submit(self._h, collection, ctypes.c_void_p(X.data_ptr()), n,
                                         ctypes.c_void_p(codes.data_ptr()),
                                         ctypes.c_void_p(factors.data_ptr()), ctypes.byref(t)))
-        self._keep[t.value] = (X, codes, factors, m.code_bytes)
+        self._keep[t.value] = (X, codes, factors, cb)
         return t.value
 
     def wait(self, ticket: int, timeout_ms: int = -1):

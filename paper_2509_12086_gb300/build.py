@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsaq.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["saq_host.cpp", "saq_encode.cu", "k_simt.cu", "k_caq.cu", "k_estimate.cu",
+SOURCES = ["saq_host.cpp", "saq_encode.cu", "k_simt.cu", "k_caq1.cu", "k_estimate.cu",
            "k_fit.cu", "k_tc.cu", "saq_noalloc.cu", "saq_ingest.cu"]
 
 

@@ -1,0 +1,264 @@
+// k_caq1.cu -- quantize, adjust and pack one kept segment with one LANE per
+// vector-segment (Sec. 3.1 Eq. find_nearest_code, Eq. adj-obj, Algorithm 1;
+// Sec. 4.2 "quantize each segment separately").
+//
+// The 32 lanes of a warp run Algorithm 1 on 32 different vectors in lockstep
+// over the coordinates of the segment: step j loads coordinate j of all 32
+// vectors (one coalesced 128-byte line of the projected rows, stored
+// interleaved by groups of 32 rows: O_i[(g * d_kept + col) * 32 + lane]) and
+// their current codes (a byte scratch with the same layout), tests +Delta then
+// -Delta for each lane against that lane's own state, and applies the lane's
+// move.  Each lane therefore executes the paper's sequential scan exactly, and
+// an accepted move costs a predicated update instead of a serialising pass.
+//
+// Decision in closed form (as in k_caq.cu): with I = <u, o> > 0,
+// S = |u|^2, u = 2c - (2^B - 1), moving u_i by 2s raises I/sqrt(S) iff
+//     s*o_i*alpha + o_i^2*beta > s*u_i + 1,   alpha = S/I, beta = S/I^2.
+// At most one of the two moves can raise the cosine (the superlevel set of the
+// cosine is a convex cone), and the paper's -Delta trial after an accepted
+// +Delta returns to the old point and is rejected.  A lane whose round made no
+// move stops (its state no longer changes).  I and S are recomputed exactly
+// for the stored factors.
+#include <algorithm>
+
+#include "saq_internal.h"
+
+namespace saq {
+
+namespace {
+
+constexpr int kU = 8;  // prefetch depth of the adjustment loop
+constexpr int kMaxSeg = 64;
+
+struct Seg {
+    int off, len, bits, words, fidx;
+    long long code_off;
+};
+struct SegTable {
+    Seg s[kMaxSeg];
+    int order[kMaxSeg];  // segments by decreasing length: long work starts first
+};
+
+// Bit-planes of one lane's segment (most significant first, 64-bit words)
+// and the exact factors.
+template <int B>
+__device__ __forceinline__ void pack_segment(const float *op, const uint8_t *cp, int len,
+                                             bool valid, uint64_t *cout, int words, float &If,
+                                             int &Si) {
+    constexpr int cmax = (1 << B) - 1;
+    uint64_t w[B];
+#pragma unroll
+    for (int p = 0; p < B; ++p) w[p] = 0ull;
+    for (int j = 0; j < len; ++j) {
+        const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
+        const int c = cp[(int64_t)j << 5];
+        const int u = 2 * c - cmax;
+        If = fmaf((float)u, x, If);
+        Si += u * u;
+        const int bp = j & 63;
+#pragma unroll
+        for (int p = 0; p < B; ++p) w[p] |= (uint64_t)((c >> (B - 1 - p)) & 1) << bp;
+        if (bp == 63 || j == len - 1) {
+            if (valid) {
+#pragma unroll
+                for (int p = 0; p < B; ++p) cout[p * words + (j >> 6)] = w[p];
+            }
+#pragma unroll
+            for (int p = 0; p < B; ++p) w[p] = 0ull;
+        }
+    }
+}
+
+// One warp per (kept segment, group of 32 rows); all kept segments of a
+// chunk in one launch.
+__global__ void __launch_bounds__(256)
+k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable t, int rounds,
+       uint8_t *__restrict__ cs, uint8_t *__restrict__ codes, int64_t code_stride,
+       float *__restrict__ factors, int nf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t groups = (n + 31) / 32;
+    if (w >= groups * nseg) return;  // uniform per warp
+    const Seg sg = t.s[t.order[w / groups]];
+    const int64_t g = w % groups;
+    const int off = sg.off, len = sg.len, B = sg.bits, words = sg.words, fidx = sg.fidx;
+    const long long code_off = sg.code_off;
+    const int cmax = (1 << B) - 1;
+    const int64_t v = g * 32 + lane;
+    const bool valid = v < n;
+    const float *op = Oi + ((g * dk + off) << 5) + lane;
+    uint8_t *cp = cs + ((g * dk + off) << 5) + lane;
+
+    float vmax = 0.f, n2 = 0.f;
+    for (int j = 0; j < len; ++j) {
+        const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
+        vmax = fmaxf(vmax, fabsf(x));
+        n2 = fmaf(x, x, n2);
+    }
+    const bool live = valid && vmax > 0.f;
+    // Eq. find_nearest_code: c = floor((o + v_max) / Delta), Delta = 2 v_max / 2^B
+    const float inv_delta = live ? (float)(1 << (B - 1)) / vmax : 0.f;
+    float I = 0.f;
+    int Si = 0;
+    for (int j = 0; j < len; ++j) {
+        const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
+        int c = 0;
+        if (live) {
+            c = (int)floorf((x + vmax) * inv_delta);
+            c = c < 0 ? 0 : (c > cmax ? cmax : c);
+        }
+        cp[(int64_t)j << 5] = (uint8_t)c;
+        const int u = 2 * c - cmax;
+        I = fmaf((float)u, x, I);
+        Si += u * u;
+    }
+    float Sf = (float)Si;
+    float rI = live ? __fdividef(1.f, I) : 0.f;
+    float alpha = Sf * rI, beta = alpha * rI;
+    bool active = live;
+    for (int r = 0; r < rounds; ++r) {
+        if (!__any_sync(0xffffffffu, active)) break;
+        bool moved = false;
+        // software pipeline: coordinates j0 + U .. j0 + 2U - 1 are loaded before
+        // j0 .. j0 + U - 1 are processed (a code is only written at its own step,
+        // so the prefetched codes are current)
+        float xb[kU];
+        int cb[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
+            cb[k] = k < len ? (int)cp[(int64_t)k << 5] : 0;
+        }
+        for (int j0 = 0; j0 < len; j0 += kU) {
+            float xn[kU];
+            int cn[kU];
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int jn = j0 + kU + k;
+                xn[k] = jn < len ? __ldg(op + ((int64_t)jn << 5)) : 0.f;
+                cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const float x = xb[k];
+                const int c = cb[k];
+                const float u = (float)(2 * c - cmax);
+                const float t = x * x * beta;
+                const bool in = active && (j0 + k < len);
+                const bool ap = in && (c < cmax) && (fmaf(x, alpha, t) > u + 1.f);
+                const bool am = in && !ap && (c > 0) && (fmaf(-x, alpha, t) > 1.f - u);
+                if (ap || am) {
+                    const float sg = ap ? 1.f : -1.f;
+                    I = fmaf(2.f * sg, x, I);
+                    Sf += fmaf(4.f * sg, u, 4.f);
+                    rI = __fdividef(1.f, I);
+                    alpha = Sf * rI;
+                    beta = alpha * rI;
+                    cp[(int64_t)(j0 + k) << 5] = (uint8_t)(ap ? c + 1 : c - 1);
+                    moved = true;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                xb[k] = xn[k];
+                cb[k] = cn[k];
+            }
+        }
+        active = active && moved;
+    }
+
+    // factors and bit-planes (most significant first, 64-bit little-endian words)
+    float If = 0.f;
+    Si = 0;
+    uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
+    switch (B) {  // uniform per warp
+        case 1: pack_segment<1>(op, cp, len, valid, cout, words, If, Si); break;
+        case 2: pack_segment<2>(op, cp, len, valid, cout, words, If, Si); break;
+        case 3: pack_segment<3>(op, cp, len, valid, cout, words, If, Si); break;
+        case 4: pack_segment<4>(op, cp, len, valid, cout, words, If, Si); break;
+        case 5: pack_segment<5>(op, cp, len, valid, cout, words, If, Si); break;
+        case 6: pack_segment<6>(op, cp, len, valid, cout, words, If, Si); break;
+        case 7: pack_segment<7>(op, cp, len, valid, cout, words, If, Si); break;
+        default: pack_segment<8>(op, cp, len, valid, cout, words, If, Si); break;
+    }
+    if (valid) {
+        float *fo = factors + v * nf;
+        if (live) {
+            const float nrm = sqrtf(n2);
+            fo[fidx] = nrm;
+            fo[fidx + 1] = If / (sqrtf((float)Si) * nrm);
+        } else {
+            // all-zero segment (the paper is silent): codes 0, |o| = 0, cos = 1
+            fo[fidx] = 0.f;
+            fo[fidx + 1] = 1.f;
+        }
+    }
+}
+
+// Row-major O (n x dk, ldo) -> interleaved O_i (groups of 32 rows).
+__global__ void k_interleave(const float *__restrict__ O, int64_t ldo, int64_t n, int dk,
+                             float *__restrict__ Oi) {
+    __shared__ float tile[32][33];
+    const int64_t g = blockIdx.y;
+    const int c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t row = g * 32 + rr;
+        const int col = c0 + tx;
+        tile[rr][tx] = (row < n && col < dk) ? O[row * ldo + col] : 0.f;
+    }
+    __syncthreads();
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int col = c0 + cc;
+        if (col < dk) Oi[((g * dk + col) << 5) + tx] = tile[tx][cc];
+    }
+}
+
+}  // namespace
+
+saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
+                       uint8_t *codes, float *factors, cudaStream_t s) {
+    const int nk = (int)m->kept.size();
+    if (n <= 0 || nk == 0) return SAQ_OK;
+    if (nk > kMaxSeg) return set_error(SAQ_ERR_UNSUPPORTED, "more than %d kept segments", kMaxSeg);
+    SegTable t;
+    for (int i = 0; i < nk; ++i) {
+        const KeptSeg &k = m->kept[(size_t)i];
+        if (k.bits < 1 || k.bits > 8)
+            return set_error(SAQ_ERR_INVALID, "segment bits %d outside 1..8", k.bits);
+        t.s[i] = Seg{k.off, k.len, k.bits, k.words, k.fidx, (long long)k.code_off};
+        t.order[i] = i;
+    }
+    std::stable_sort(t.order, t.order + nk, [&](int a, int b) { return t.s[a].len > t.s[b].len; });
+    const int64_t warps = (n + 31) / 32 * nk;
+    const int64_t blocks = (warps + 7) / 8;
+    k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, m->dk, nk, t, m->rounds, cs, codes,
+                                            (int64_t)m->code_bytes, factors, m->nf);
+    note_launches();
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return SAQ_OK;
+}
+
+saq_status launch_interleave(const float *O, int64_t ldo, int64_t n, int dk, float *Oi,
+                             cudaStream_t s) {
+    if (n <= 0 || dk <= 0) return SAQ_OK;
+    const int64_t groups = (n + 31) / 32;
+    dim3 grid((unsigned)((dk + 31) / 32), (unsigned)groups);
+    if (groups > 65535) {
+        // split along groups to respect the grid's y limit
+        for (int64_t g0 = 0; g0 < groups; g0 += 65535) {
+            const int64_t gn = std::min<int64_t>(65535, groups - g0);
+            dim3 gg((unsigned)((dk + 31) / 32), (unsigned)gn);
+            k_interleave<<<gg, dim3(32, 8), 0, s>>>(O + g0 * 32 * ldo, ldo, n - g0 * 32, dk,
+                                                    Oi + g0 * 32 * (int64_t)dk);
+            note_launches();
+        }
+    } else {
+        k_interleave<<<grid, dim3(32, 8), 0, s>>>(O, ldo, n, dk, Oi);
+        note_launches();
+    }
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return SAQ_OK;
+}
+
+}  // namespace saq

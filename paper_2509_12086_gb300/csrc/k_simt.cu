@@ -16,7 +16,7 @@ constexpr int kBM = 128, kBN = 128, kBK = 8;
 __global__ void __launch_bounds__(256)
 k_project_simt(const float *__restrict__ X, int64_t n, int d,
                const float *__restrict__ c, const float *__restrict__ W, int dk,
-               float *__restrict__ O, int64_t ldo) {
+               float *__restrict__ O, int64_t ldo, int il) {
     __shared__ float As[kBK][kBM + 4];
     __shared__ float Bs[kBK][kBN + 4];
     const int tid = threadIdx.x;
@@ -65,7 +65,10 @@ k_project_simt(const float *__restrict__ X, int64_t n, int d,
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int gj = col0 + tx + 16 * j;
-            if (gj < dk) O[gi * ldo + gj] = acc[i][j];
+            if (gj < dk) {
+                if (il) O[(((gi >> 5) * dk + gj) << 5) + (gi & 31)] = acc[i][j];
+                else O[gi * ldo + gj] = acc[i][j];
+            }
         }
     }
 }
@@ -96,13 +99,15 @@ __global__ void k_copy_strided(const float *__restrict__ src, int64_t ss,
 }  // namespace
 
 saq_status launch_project_simt(const saq_model *m, const float *X, int64_t n,
-                               float *O, int64_t ldo, cudaStream_t s) {
+                               float *O, int64_t ldo, int layout, cudaStream_t s) {
     if (n <= 0 || m->dk <= 0) return SAQ_OK;
+    // kBM * 65535 is a multiple of 32, so interleaved chunks start on a group
     for (int64_t r0 = 0; r0 < n; r0 += (int64_t)kBM * 65535) {
         const int64_t rows = n - r0 < (int64_t)kBM * 65535 ? n - r0 : (int64_t)kBM * 65535;
         dim3 grid((unsigned)((rows + kBM - 1) / kBM), (unsigned)((m->dk + kBN - 1) / kBN));
+        float *Ob = layout == kInterleaved ? O + r0 * m->dk : O + r0 * ldo;
         k_project_simt<<<grid, 256, 0, s>>>(X + r0 * m->d, rows, m->d, m->d_mean, m->d_W,
-                                            m->dk, O + r0 * ldo, ldo);
+                                            m->dk, Ob, ldo, layout == kInterleaved ? 1 : 0);
         note_launches();
     }
     SAQ_CUDA_CHECK(cudaGetLastError());

@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmb0,
           const __grid_constant__ CUtensorMap tmb1, int64_t n, int dk, int npass, int nkb,
           const float *__restrict__ mean_pad, float x_scale, const float *__restrict__ col_scale,
-          float *__restrict__ O, int64_t ldo, float *__restrict__ norms, int64_t nstride,
-          int *__restrict__ err) {
+          float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms,
+          int64_t nstride, int *__restrict__ err) {
     using C = Cfg<MODE>;
     constexpr uint32_t SB = stage_bytes<MODE>();
     extern __shared__ uint8_t smem_raw[];
@@ -381,6 +381,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
         if (ready) {
             tc_fence_after();
             float *orow = O + (row0 + r) * ldo;
+            // interleaved: column `col` of row R at ((R / 32) * dk + col) * 32 + R % 32
+            float *ogrp = O + (((row0 + r) >> 5) * (int64_t)dk << 5) + lane;
             const bool vec = ((ldo & 3) == 0) && ((((uintptr_t)O) & 15) == 0);
 #pragma unroll 1
             for (int c = 0; c < kNP; c += 16) {
@@ -390,7 +392,9 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
                 if (!row_ok || col >= dk) continue;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] *= col_scale[col + i];
-                if (vec && col + 16 <= dk) {
+                if (il) {
+                    for (int i = 0; i < 16 && col + i < dk; ++i) ogrp[(int64_t)(col + i) << 5] = v[i];
+                } else if (vec && col + 16 <= dk) {
 #pragma unroll
                     for (int i = 0; i < 16; i += 4)
                         *reinterpret_cast<float4 *>(orow + col + i) =
@@ -463,8 +467,8 @@ struct TcExtra {
 double pow2_near(double x) { return ldexp(1.0, (int)lround(log2(x))); }
 
 template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, int64_t n,
-                                           float *O, int64_t ldo, float *norms, int64_t ns,
-                                           cudaStream_t s) {
+                                           float *O, int64_t ldo, int layout, float *norms,
+                                           int64_t ns, cudaStream_t s) {
     const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
     CUtensorMap tmx;
     saq_status st = make_map(&tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, (uint64_t)m->d,
@@ -479,7 +483,7 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
     if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
     k_proj_tc<MODE><<<(unsigned)blocks, kThreads, smem_bytes<MODE>(), s>>>(
         tmx, ex->b0, ex->b1, n, m->dk, npass, nkb, ex->mean_pad, ex->x_scale, m->tc.col_scale, O,
-        ldo, norms, ns, ex->err);
+        ldo, layout == kInterleaved ? 1 : 0, norms, ns, ex->err);
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
@@ -598,13 +602,17 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
 }
 
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, float *O,
-                             int64_t ldo, float *norms2, int64_t norms_stride, cudaStream_t s) {
+                             int64_t ldo, int layout, float *norms2, int64_t norms_stride,
+                             cudaStream_t s) {
     if (n <= 0) return SAQ_OK;
     if (((uintptr_t)X & 15u) != 0) return set_error(SAQ_ERR_INVALID, "X not 16-byte aligned");
     switch (m->tc.precision) {
-        case SAQ_PREC_FP32: return launch_mode<kSplit>(m, X, n, O, ldo, norms2, norms_stride, s);
-        case SAQ_PREC_BF16: return launch_mode<kBF16>(m, X, n, O, ldo, norms2, norms_stride, s);
-        case SAQ_PREC_FP8: return launch_mode<kFP8>(m, X, n, O, ldo, norms2, norms_stride, s);
+        case SAQ_PREC_FP32:
+            return launch_mode<kSplit>(m, X, n, O, ldo, layout, norms2, norms_stride, s);
+        case SAQ_PREC_BF16:
+            return launch_mode<kBF16>(m, X, n, O, ldo, layout, norms2, norms_stride, s);
+        case SAQ_PREC_FP8:
+            return launch_mode<kFP8>(m, X, n, O, ldo, layout, norms2, norms_stride, s);
     }
     return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
 }

@@ -35,33 +35,39 @@ bool use_tc(const saq_model *m) {
 
 }  // namespace
 
-// Projection of rows [0, n) into O (ldo) and |x - c|^2 into norms (stride).
+size_t encode_scratch_bytes(const saq_model *m, int64_t rows) {
+    const size_t elems = (size_t)((rows + 31) / 32 * 32) * (size_t)std::max(1, m->dk);
+    return ((elems * sizeof(float) + 255) & ~(size_t)255) + ((elems + 255) & ~(size_t)255);
+}
+
+// Projection of rows [0, n) into O and |x - c|^2 into norms (stride).
 saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                        float *norms, int64_t nstride, cudaStream_t s) {
-    if (use_tc(m)) return launch_project_tc(m, X, n, O, ldo, norms, nstride, s);
-    saq_status st = launch_project_simt(m, X, n, O, ldo, s);
+                        int layout, float *norms, int64_t nstride, cudaStream_t s) {
+    if (use_tc(m)) return launch_project_tc(m, X, n, O, ldo, layout, norms, nstride, s);
+    saq_status st = launch_project_simt(m, X, n, O, ldo, layout, s);
     if (st != SAQ_OK) return st;
     return launch_rownorm2(m, X, n, norms, nstride, s);
 }
 
-saq_status quantize_rows(const saq_model *m, const float *O, int64_t ldo, int64_t n,
+// Quantize rows [0, n) whose interleaved projection sits at the start of
+// `scratch` (sized by encode_scratch_bytes for rows_cap rows).
+saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, int64_t n,
                          uint8_t *codes, float *factors, cudaStream_t s) {
-    for (size_t k = 0; k < m->kept.size(); ++k) {
-        saq_status st = launch_caq_segment(m, (int)k, O, ldo, n, codes, factors, s);
-        if (st != SAQ_OK) return st;
-    }
-    return SAQ_OK;
+    const size_t elems = (size_t)((rows_cap + 31) / 32 * 32) * (size_t)std::max(1, m->dk);
+    float *Oi = static_cast<float *>(scratch);
+    uint8_t *cs = static_cast<uint8_t *>(scratch) + ((elems * sizeof(float) + 255) & ~(size_t)255);
+    return launch_caq1(m, Oi, n, cs, codes, factors, s);
 }
 
-// The whole encode of rows [0, n) on stream s with O scratch of `rows` rows.
+// The whole encode of rows [0, n) on stream s with a scratch for `rows` rows.
 saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
-                       float *factors, float *O, int64_t rows, cudaStream_t s) {
+                       float *factors, void *scratch, int64_t rows, cudaStream_t s) {
     for (int64_t r0 = 0; r0 < n; r0 += rows) {
         const int64_t nr = std::min(rows, n - r0);
-        saq_status st = project_rows(m, X + r0 * m->d, nr, O, m->dk, factors + r0 * m->nf,
-                                     m->nf, s);
+        saq_status st = project_rows(m, X + r0 * m->d, nr, static_cast<float *>(scratch), m->dk,
+                                     kInterleaved, factors + r0 * m->nf, m->nf, s);
         if (st != SAQ_OK) return st;
-        st = quantize_rows(m, O, m->dk, nr, codes + r0 * (int64_t)m->code_bytes,
+        st = quantize_rows(m, scratch, rows, nr, codes + r0 * (int64_t)m->code_bytes,
                            factors + r0 * m->nf, s);
         if (st != SAQ_OK) return st;
     }
@@ -89,12 +95,12 @@ saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n, uint8_t
     cudaStream_t s = (cudaStream_t)stream;
     if (m->dk == 0) return launch_rownorm2(m, X_dev, n, factors_dev, m->nf, s);
     const int64_t rows = chunk_rows(m, n, (size_t)512 << 20);
-    float *O = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&O, sizeof(float) * (size_t)rows * m->dk, s);
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, encode_scratch_bytes(m, rows), s);
     if (e != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
-    st = encode_rows(m, X_dev, n, codes_dev, factors_dev, O, rows, s);
-    cudaFreeAsync(O, s);
+    st = encode_rows(m, X_dev, n, codes_dev, factors_dev, scratch, rows, s);
+    cudaFreeAsync(scratch, s);
     return st;
 }
 
@@ -110,7 +116,8 @@ saq_status saq_project(const saq_model *m, const float *X_dev, int64_t n, float 
         return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
     saq_status st = check_device(m);
     if (st != SAQ_OK) return st;
-    return project_rows(m, X_dev, n, O_dev, m->dk, norms2_dev, 1, (cudaStream_t)stream);
+    return project_rows(m, X_dev, n, O_dev, m->dk, kRowMajor, norms2_dev, 1,
+                        (cudaStream_t)stream);
 }
 
 saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
@@ -128,8 +135,15 @@ saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
     if (st != SAQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     st = launch_copy_strided(norms2_dev, 1, factors_dev, m->nf, n, s);
-    if (st != SAQ_OK) return st;
-    return quantize_rows(m, O_dev, m->dk, n, codes_dev, factors_dev, s);
+    if (st != SAQ_OK || m->dk == 0) return st;
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, encode_scratch_bytes(m, n), s);
+    if (e != cudaSuccess)
+        return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
+    st = launch_interleave(O_dev, m->dk, n, m->dk, static_cast<float *>(scratch), s);
+    if (st == SAQ_OK) st = quantize_rows(m, scratch, n, n, codes_dev, factors_dev, s);
+    cudaFreeAsync(scratch, s);
+    return st;
 }
 
 saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
@@ -150,9 +164,9 @@ saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
     const size_t xb = sizeof(float) * (size_t)rows * m->d;
     const size_t cb = m->code_bytes * (size_t)rows;
     const size_t fb = sizeof(float) * (size_t)rows * m->nf;
-    const size_t ob = sizeof(float) * (size_t)rows * std::max(1, m->dk);
+    const size_t ob = encode_scratch_bytes(m, rows);
     uint8_t *buf[2] = {nullptr, nullptr};
-    float *O = nullptr;
+    void *O = nullptr;
     cudaStream_t cs[2] = {nullptr, nullptr};
     cudaEvent_t in_done[2] = {nullptr, nullptr}, enc_done[2] = {nullptr, nullptr},
                 out_done[2] = {nullptr, nullptr};
@@ -252,7 +266,7 @@ saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
         return set_error(SAQ_ERR_OOM, "scratch allocation failed");
     }
     // queries are rotated with the FP32 CUDA-core projection
-    st = launch_project_simt(m, Q_dev, nq, qrot, m->dk, s);
+    st = launch_project_simt(m, Q_dev, nq, qrot, m->dk, kRowMajor, s);
     if (st == SAQ_OK) st = launch_rownorm2(m, Q_dev, nq, qn2, 1, s);
     if (st == SAQ_OK)
         st = launch_estimate(m, codes_dev, factors_dev, n, qrot, qn2, nq, prefix_bits, vs,

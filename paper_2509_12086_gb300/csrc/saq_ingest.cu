@@ -39,7 +39,8 @@ struct Piece {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    float *X = nullptr, *factors = nullptr, *O = nullptr;
+    float *X = nullptr, *factors = nullptr;
+    void *O = nullptr;
     uint8_t *codes = nullptr;
     bool busy = false;
     bool finished = false;  // set by the stream callback
@@ -88,11 +89,14 @@ void CUDART_CB on_batch_done(void *arg) {
 void reap(saq_ingest *s) {
     for (Slot &sl : s->slots) {
         if (!sl.busy || !sl.finished) continue;
+        // the callback fired, so the batch's copies and kernels are done; the
+        // callback itself may still be returning (not-ready is no error)
         const cudaError_t e = cudaStreamQuery(sl.stream);
+        const bool failed = e != cudaSuccess && e != cudaErrorNotReady;
         const Clock::time_point now = Clock::now();
         for (const Piece &pc : sl.pieces) {
             Request *r = pc.req;
-            if (e != cudaSuccess) r->status = SAQ_ERR_CUDA;
+            if (failed) r->status = SAQ_ERR_CUDA;
             r->rows_done += pc.nr;
             if (r->rows_done == r->n && !r->done) {
                 r->done = true;
@@ -224,7 +228,7 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
     int dev = 0;
     SAQ_CUDA_CHECK(cudaGetDevice(&dev));
     int dmax = 0, dkmax = 0, nfmax = 0;
-    size_t cbmax = 0;
+    size_t cbmax = 0, scrmax = 0;
     for (int32_t i = 0; i < n_models; ++i) {
         if (!models[i]) return set_error(SAQ_ERR_INVALID, "collection %d is NULL", i);
         if (models[i]->device != dev)
@@ -233,10 +237,11 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
         dkmax = std::max(dkmax, models[i]->dk);
         nfmax = std::max(nfmax, models[i]->nf);
         cbmax = std::max(cbmax, models[i]->code_bytes);
+        scrmax = std::max(scrmax, saq::encode_scratch_bytes(models[i], p->max_batch_rows));
     }
     const size_t rows = (size_t)p->max_batch_rows;
-    const size_t per_slot = rows * (sizeof(float) * ((size_t)dmax + (size_t)std::max(1, dkmax) + nfmax) +
-                                    cbmax) + 4 * 256;
+    const size_t per_slot = rows * (sizeof(float) * ((size_t)dmax + nfmax) + cbmax) + scrmax +
+                            4 * 256;
     if (per_slot * (size_t)p->slots > p->hbm_budget_bytes)
         return set_error(SAQ_ERR_OOM,
                          "%d slots of %zu bytes exceed the HBM budget of %zu bytes", p->slots,
@@ -253,7 +258,7 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
             cudaMalloc(&sl.X, sizeof(float) * rows * dmax) != cudaSuccess ||
             cudaMalloc(&sl.codes, std::max<size_t>(16, cbmax * rows)) != cudaSuccess ||
             cudaMalloc(&sl.factors, sizeof(float) * rows * nfmax) != cudaSuccess ||
-            cudaMalloc(&sl.O, sizeof(float) * rows * std::max(1, dkmax)) != cudaSuccess) {
+            cudaMalloc(&sl.O, scrmax) != cudaSuccess) {
             free_slots(s);
             delete s;
             return set_error(SAQ_ERR_OOM, "slot allocation failed");

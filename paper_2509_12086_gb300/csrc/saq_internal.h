@@ -87,12 +87,16 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t s);
 void model_release_device(saq_model *m);
 
 // ---------------------------------------------------------------- kernels
+// Layout of projected rows: row-major (ldo floats per row) or interleaved by
+// groups of 32 rows, O_i[((row / 32) * dk + col) * 32 + row % 32] (the layout
+// the quantize kernel reads; ldo is ignored).
+enum { kRowMajor = 0, kInterleaved = 1 };
 // O[i, :] = W (x_i - c) for rows [0, n): FP32 SIMT GEMM, exact FP32 products.
 saq_status launch_project_simt(const saq_model *m, const float *X, int64_t n,
-                               float *O, int64_t ldo, cudaStream_t s);
+                               float *O, int64_t ldo, int layout, cudaStream_t s);
 // Tensor-core projection (tcgen05 + TMA); precision from m->tc.
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n,
-                             float *O, int64_t ldo, float *norms2,
+                             float *O, int64_t ldo, int layout, float *norms2,
                              int64_t norms_stride, cudaStream_t s);
 bool tc_supported(const saq_model *m);
 void tc_release(saq_model *m);
@@ -105,18 +109,25 @@ saq_status launch_rownorm2(const saq_model *m, const float *X, int64_t n,
 // Strided copy of n floats.
 saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
                                int64_t dstride, int64_t n, cudaStream_t s);
-// Quantize + adjust + pack one kept segment for rows [0, n) of O.
-saq_status launch_caq_segment(const saq_model *m, int seg, const float *O,
-                              int64_t ldo, int64_t n, uint8_t *codes,
-                              float *factors, cudaStream_t s);
-// Projection and quantization of rows [0, n) (saq_encode.cu).
+// Quantize + adjust + pack every kept segment for rows [0, n) of interleaved
+// projected rows Oi, with a byte scratch cs of the same layout (k_caq1.cu).
+saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
+                       uint8_t *codes, float *factors, cudaStream_t s);
+// Row-major O -> interleaved Oi.
+saq_status launch_interleave(const float *O, int64_t ldo, int64_t n, int dk, float *Oi,
+                             cudaStream_t s);
+// Scratch of an encode of up to `rows` rows: the interleaved projected rows
+// (FP32) followed by the byte code scratch (saq_encode.cu).
+size_t encode_scratch_bytes(const saq_model *m, int64_t rows);
+// Projection of rows [0, n) (saq_encode.cu).
 saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                        float *norms, int64_t nstride, cudaStream_t s);
-saq_status quantize_rows(const saq_model *m, const float *O, int64_t ldo, int64_t n,
+                        int layout, float *norms, int64_t nstride, cudaStream_t s);
+// Quantization of rows [0, n) from interleaved projected rows in `scratch`.
+saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, int64_t n,
                          uint8_t *codes, float *factors, cudaStream_t s);
-// The whole encode of rows [0, n) with O scratch of `rows` rows (saq_encode.cu).
+// The whole encode of rows [0, n) with a scratch for `rows` rows.
 saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
-                       float *factors, float *O, int64_t rows, cudaStream_t s);
+                       float *factors, void *scratch, int64_t rows, cudaStream_t s);
 // Estimator.
 saq_status launch_estimate(const saq_model *m, const uint8_t *codes,
                            const float *factors, int64_t n, const float *Qrot,

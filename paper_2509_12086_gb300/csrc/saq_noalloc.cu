@@ -8,9 +8,10 @@
 
 namespace {
 
-// 32 MiB of FP32 scratch: the projected rows of one call.
-constexpr size_t kScratchFloats = (size_t)8 << 20;
-static __device__ __align__(256) float g_noalloc_scratch[kScratchFloats];
+// 32 MiB of scratch: the projected rows of one call (FP32) and their codes
+// during adjustment (one byte each), i.e. 5 bytes per row and kept dimension.
+constexpr size_t kScratchBytes = (size_t)32 << 20;
+static __device__ __align__(256) float g_noalloc_scratch[kScratchBytes / sizeof(float)];
 
 // In host code g_noalloc_scratch names a host-side stand-in, not device
 // memory; the device address is looked up once per device.
@@ -48,12 +49,14 @@ extern "C" saq_status saq_encode_noalloc(const saq_model *m, const float *X_dev,
         return set_error(SAQ_ERR_INVALID, "NULL buffer");
     if (((uintptr_t)X_dev | (uintptr_t)codes_dev | (uintptr_t)factors_dev) & 15u)
         return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
-    if ((double)n * (double)m->dk > (double)kScratchFloats)
+    if (encode_scratch_bytes(m, n) > kScratchBytes) {
+        int64_t most = 0;
+        while (encode_scratch_bytes(m, most + 32) <= kScratchBytes) most += 32;
         return set_error(SAQ_ERR_INVALID,
                          "n = %lld rows x d_kept = %d exceeds the no-allocation scratch of "
-                         "%zu floats (at most %lld rows for this model)",
-                         (long long)n, m->dk, kScratchFloats,
-                         (long long)(m->dk > 0 ? (int64_t)kScratchFloats / m->dk : 0));
+                         "%zu bytes (at most %lld rows for this model)",
+                         (long long)n, m->dk, kScratchBytes, (long long)most);
+    }
     int dev = -1;
     SAQ_CUDA_CHECK(cudaGetDevice(&dev));
     if (dev != m->device)
@@ -64,7 +67,5 @@ extern "C" saq_status saq_encode_noalloc(const saq_model *m, const float *X_dev,
     float *O = nullptr;
     saq_status st = scratch_address(dev, &O);
     if (st != SAQ_OK) return st;
-    st = project_rows(m, X_dev, n, O, m->dk, factors_dev, m->nf, s);
-    if (st != SAQ_OK) return st;
-    return quantize_rows(m, O, m->dk, n, codes_dev, factors_dev, s);
+    return encode_rows(m, X_dev, n, codes_dev, factors_dev, O, n, s);
 }

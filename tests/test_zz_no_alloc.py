@@ -52,9 +52,17 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     torch.cuda.set_device(0)
     d = 960
     model = P.saq_fit(synth.power_law(5000, d, 0.8, device="cuda"), avg_bits=4.0)
-    max_rows = (8 << 20) // model.d_kept
-    X = torch.zeros((max_rows + 1, d), device="cuda")
-    codes, factors = model.alloc_outputs(max_rows + 1)
+    assert model.d_kept == 960
+    # 32 MiB holds 5 bytes per row and kept dimension, rows in groups of 32:
+    # 218 groups = 6,976 rows fit at d_kept = 960, one more row does not
+    X = synth.power_law(6977, d, 0.8, seed=303, device="cuda")
+    codes, factors = model.alloc_outputs(6977)
     rc = _call_noalloc(model, X, codes, factors)
     assert rc == 1
-    assert b"exceeds the no-allocation scratch" in P.load().saq_last_error()
+    msg = P.load().saq_last_error()
+    assert b"exceeds the no-allocation scratch" in msg and b"at most 6976 rows" in msg
+    rc = _call_noalloc(model, X[:6976], codes[:6976], factors[:6976])
+    assert rc == 0, P.load().saq_last_error()
+    ref_codes, ref_factors = model.encode(X[:6976].contiguous())
+    torch.cuda.synchronize()
+    assert torch.equal(codes[:6976, :model.code_bytes], ref_codes)
