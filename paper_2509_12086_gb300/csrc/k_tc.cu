@@ -1,16 +1,21 @@
 // k_tc.cu -- tensor-core projection O = (X - c) W^T on sm_103a (Sec. 3.1
 // Eq. rotate with the combined PCA + segment-rotation matrix of Sec. 5.1).
 //
-// One CTA computes a 128-row x 128-column tile of O over the full K = d:
-//   warp 0      TMA producer: X tile (FP32, 128 x BK, 128-byte swizzle,
-//               staged) and the W operand tile(s) for the stage;
-//   warp 1      TMEM owner and MMA issuer (one elected lane): tcgen05.mma
-//               with the accumulator (128 lanes x 128 FP32 columns) in TMEM;
-//   warps 2-5   converters, then epilogue.  Thread <-> tile row: the thread
-//               reads its row of the staged X tile, centres it (x - c),
-//               converts it into the A operand(s) in the UMMA K-major
-//               128-byte-swizzled layout, and accumulates |x - c|^2; after the
-//               K loop it reads its accumulator row back with tcgen05.ld.
+// One CTA computes a 128-row x NP-column tile of O (NP <= 256, a multiple of
+// 16 chosen per model so that the column passes are balanced) over K = d:
+//   warp 0      TMA producer: the FP32 X tile (128 rows x 32 values per box,
+//               128-byte swizzle, staged) and the W operand tile(s);
+//   warp 1      TMEM owner and MMA issuer (one elected lane): tcgen05.mma,
+//               accumulator 128 lanes x NP FP32 columns in TMEM;
+//   warps 2-9   converters, then epilogue.  Two threads per tile row (one per
+//               half of the K block): read the staged X values, centre and
+//               scale them with one FMA against -c*s kept in shared memory,
+//               convert them into the A operand(s) (UMMA K-major, 64-byte
+//               rows, 64-byte swizzle) and accumulate |x - c|^2; after the K
+//               loop each warp drains its TMEM lane quadrant for half of the
+//               columns with tcgen05.ld.
+// Operand rows are 64 bytes per stage (32 FP16/BF16 or 64 E4M3 values), so
+// three or more stages fit in shared memory.
 // Precision modes:
 //   kSplit  FP32: A = a_hi + a_lo and B = b_hi + b_lo as FP16 pairs (scaled by
 //           powers of two), D = a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32
@@ -39,28 +44,36 @@ namespace {
 
 enum Mode { kSplit = 0, kBF16 = 1, kFP8 = 2 };
 
-constexpr int kBM = 128;           // rows per tile (UMMA M)
-constexpr int kNP = 128;           // output columns per tile (UMMA N)
-constexpr int kTmemCols = 128;
-constexpr int kThreads = 192;
-constexpr uint32_t kTile = 16384;  // one 128 x 128-byte operand / staging tile
+constexpr int kBM = 128;            // rows per tile (UMMA M)
+constexpr int kNPMax = 256;         // output columns per tile at most (UMMA N)
+constexpr int kTmemCols = 256;
+constexpr int kConvWarps = 8;
+constexpr int kThreads = 64 + 32 * kConvWarps;
+constexpr uint32_t kXBox = 16384;   // 128 rows x 128 bytes of staged FP32
+constexpr uint32_t kATile = 8192;   // 128 rows x 64 bytes
+constexpr uint32_t kBTile = 16384;  // 256 rows x 64 bytes
 
 template <int MODE> struct Cfg;
-template <> struct Cfg<kSplit> {
-    static constexpr int BK = 64, STAGES = 2, NA = 2, XBOX = 2;
+template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage
+    static constexpr int BK = 32, STAGES = 3, NA = 2, XBOX = 1;
 };
 template <> struct Cfg<kBF16> {
-    static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2;
+    static constexpr int BK = 32, STAGES = 4, NA = 1, XBOX = 1;
 };
-template <> struct Cfg<kFP8> {
-    static constexpr int BK = 128, STAGES = 2, NA = 1, XBOX = 4;
+template <> struct Cfg<kFP8> {  // 64 E4M3 per row per stage
+    static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2;
 };
 
 template <int MODE> constexpr uint32_t stage_bytes() {
-    return (uint32_t)(Cfg<MODE>::XBOX + 2 * Cfg<MODE>::NA) * kTile;
+    return (uint32_t)Cfg<MODE>::XBOX * kXBox + (uint32_t)Cfg<MODE>::NA * (kATile + kBTile);
 }
-template <int MODE> constexpr uint32_t smem_bytes() {
-    return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 /*align*/ + 256 /*barriers*/;
+template <int MODE> constexpr uint32_t a_offset() { return (uint32_t)Cfg<MODE>::XBOX * kXBox; }
+template <int MODE> constexpr uint32_t b_offset() {
+    return a_offset<MODE>() + (uint32_t)Cfg<MODE>::NA * kATile;
+}
+// dynamic shared memory: stages, barriers and the row-norm halves, -c*s
+template <int MODE> uint32_t smem_bytes(int dpad) {
+    return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + 640 + 4u * (uint32_t)dpad;
 }
 
 // ------------------------------------------------------------- PTX helpers
@@ -129,20 +142,20 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
+// K-major operand, 64-byte rows with the 64-byte swizzle, 8-row groups 512
+// bytes apart.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-    d |= (uint64_t)1 << 46;            // descriptor version
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    d |= (uint64_t)1 << 16;           // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;           // descriptor version
+    d |= (uint64_t)4 << 61;           // 64-byte swizzle
     return d;
 }
-template <int MODE> __device__ __forceinline__ constexpr uint32_t umma_idesc() {
+template <int MODE> __host__ __device__ constexpr uint32_t umma_idesc_base() {
     uint32_t d = 1u << 4;                           // accumulate in FP32
     if (MODE == kBF16) d |= (1u << 7) | (1u << 10);  // A, B = BF16 (F16 and E4M3 encode as 0)
-    d |= (uint32_t)(kNP >> 3) << 17;
     d |= (uint32_t)(kBM >> 4) << 24;
     return d;
 }
@@ -180,23 +193,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void named_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
 
 __device__ __forceinline__ uint32_t pack_h2(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 __device__ __forceinline__ uint32_t pack_b2(__nv_bfloat162 h) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// Offset of 16-byte chunk `c` of row `r` in a 128-row x 128-byte tile with
-// the 128-byte swizzle (chunk index XOR row mod 8).
-__device__ __forceinline__ uint32_t swz(int r, int c) {
+// 16-byte chunk `c` of row `r`: staged FP32 (128-byte rows, 128-byte swizzle)
+// and operand tiles (64-byte rows, 64-byte swizzle).
+__device__ __forceinline__ uint32_t swz128(int r, int c) {
     return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ uint32_t swz64(int r, int c) {
+    return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmb0,
-          const __grid_constant__ CUtensorMap tmb1, int64_t n, int dk, int npass, int nkb,
-          const float *__restrict__ mean_pad, float x_scale, const float *__restrict__ col_scale,
+          const __grid_constant__ CUtensorMap tmb1, int64_t n, int dk, int npass, int np, int nkb,
+          const float *__restrict__ mcs_g, float x_scale, const float *__restrict__ col_scale,
           float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms,
           int64_t nstride, int *__restrict__ err) {
     using C = Cfg<MODE>;
@@ -209,17 +228,20 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
     uint64_t *accf = empty + C::STAGES;
     uint32_t *tmem_slot = (uint32_t *)(accf + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *nrm_half = (float *)(smem + C::STAGES * SB + 128);   // 128 floats
+    float *mcs = (float *)(smem + C::STAGES * SB + 128 + 512);  // nkb * BK floats
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tile = blockIdx.x / npass;
     const int pass = (int)(blockIdx.x % npass);
     const int64_t row0 = tile * kBM;
-    const int col0 = pass * kNP;
+    const int col0 = pass * np;
 
+    for (int k = threadIdx.x; k < nkb * C::BK; k += kThreads) mcs[k] = mcs_g[k];
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&conv[s], 4);
+            mbar_init(&conv[s], kConvWarps);
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
@@ -242,19 +264,20 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmx) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmb0) : "memory");
+            const uint32_t tx = (uint32_t)C::XBOX * kXBox + (uint32_t)C::NA * (uint32_t)np * 64u;
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % C::STAGES;
                 const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 1)) break;
                 uint8_t *st = smem + s * SB;
-                mbar_expect_tx(&full[s], (uint32_t)(C::XBOX + C::NA) * kTile);
+                mbar_expect_tx(&full[s], tx);
 #pragma unroll
                 for (int b = 0; b < C::XBOX; ++b)
-                    tma_load_2d(st + b * kTile, &tmx, kb * C::BK + b * 32, (int)row0, &full[s]);
-                uint8_t *bs = st + (C::XBOX + C::NA) * kTile;
+                    tma_load_2d(st + b * kXBox, &tmx, kb * C::BK + b * 32, (int)row0, &full[s]);
+                uint8_t *bs = st + b_offset<MODE>();
                 tma_load_2d(bs, &tmb0, kb * C::BK, col0, &full[s]);
-                if (C::NA == 2) tma_load_2d(bs + kTile, &tmb1, kb * C::BK, col0, &full[s]);
+                if (C::NA == 2) tma_load_2d(bs + kBTile, &tmb1, kb * C::BK, col0, &full[s]);
                 issued = kb + 1;
             }
             // drain: the last loads of each stage must land before the CTA exits
@@ -268,21 +291,20 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = umma_idesc<MODE>();
-            constexpr int KSTEPS = 4;  // 32-byte K steps per 128-byte row
+            const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(np >> 3) << 17);
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % C::STAGES;
                 const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
                 if (!mbar_wait(&conv[s], ph, abort_flag, err, 2)) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + s * SB);
-                const uint64_t a0 = umma_desc(st + C::XBOX * kTile);
-                const uint64_t a1 = umma_desc(st + (C::XBOX + 1) * kTile);
-                const uint64_t b0 = umma_desc(st + (C::XBOX + C::NA) * kTile);
-                const uint64_t b1 = umma_desc(st + (C::XBOX + C::NA + 1) * kTile);
+                const uint64_t a0 = umma_desc(st + a_offset<MODE>());
+                const uint64_t a1 = umma_desc(st + a_offset<MODE>() + kATile);
+                const uint64_t b0 = umma_desc(st + b_offset<MODE>());
+                const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
 #pragma unroll
-                for (int kk = 0; kk < KSTEPS; ++kk) {
-                    const uint64_t off = (uint64_t)(kk * 2);  // 32 bytes >> 4
+                for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
+                    const uint64_t off = (uint64_t)(kk * 2);
                     umma<MODE>(tmem, a0 + off, b0 + off, idesc, (kb | kk) != 0);
                     if (C::NA == 2) {
                         umma<MODE>(tmem, a0 + off, b1 + off, idesc, 1u);
@@ -295,9 +317,10 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
         }
         __syncwarp();
     } else {
-        // ---- converters (one tile row per thread)
+        // ---- converters: two threads per tile row, one per half of a K block
         const int q = warp & 3;
         const int r = q * 32 + lane;
+        const int h = (warp - 2) >> 2;
         const bool row_ok = row0 + r < n;
         float nrm = 0.f;
         bool ok = true;
@@ -309,63 +332,66 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) { ok = false; break; }
             uint8_t *st = smem + s * SB;
-            uint8_t *a0 = st + C::XBOX * kTile;
-            const float *mk = mean_pad + (size_t)kb * C::BK;
+            uint8_t *a0 = st + a_offset<MODE>();
+            const float *mk = mcs + kb * C::BK;
             if (MODE == kFP8) {
-                // 8 chunks of 16 E4M3 values = 4 staging chunks of 4 FP32 each
+                // 2 chunks of 16 E4M3 (32 values) per thread, all from staged box h
 #pragma unroll
-                for (int ac = 0; ac < 8; ++ac) {
-                    const uint8_t *xb = st + (ac >> 1) * kTile;
+                for (int i = 0; i < 2; ++i) {
+                    const int ac = 2 * h + i;  // operand chunk: values ac*16 .. ac*16+15
+                    const uint8_t *xb = st + h * kXBox;
                     uint32_t w[4];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int c = (ac & 1) * 4 + h;
-                        const float4 x = *reinterpret_cast<const float4 *>(xb + swz(r, c));
-                        const float4 m = *reinterpret_cast<const float4 *>(mk + ac * 16 + h * 4);
-                        const float y0 = x.x - m.x, y1 = x.y - m.y, y2 = x.z - m.z, y3 = x.w - m.w;
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = i * 4 + e;  // staged chunk within box h
+                        const float4 x = *reinterpret_cast<const float4 *>(xb + swz128(r, c));
+                        const float4 m = *reinterpret_cast<const float4 *>(mk + ac * 16 + e * 4);
+                        const float y0 = fmaf(x.x, x_scale, m.x), y1 = fmaf(x.y, x_scale, m.y);
+                        const float y2 = fmaf(x.z, x_scale, m.z), y3 = fmaf(x.w, x_scale, m.w);
                         nrm = fmaf(y0, y0, nrm); nrm = fmaf(y1, y1, nrm);
                         nrm = fmaf(y2, y2, nrm); nrm = fmaf(y3, y3, nrm);
                         const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
-                            make_float2(y0 * x_scale, y1 * x_scale), __NV_SATFINITE, __NV_E4M3);
+                            make_float2(y0, y1), __NV_SATFINITE, __NV_E4M3);
                         const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-                            make_float2(y2 * x_scale, y3 * x_scale), __NV_SATFINITE, __NV_E4M3);
-                        w[h] = (uint32_t)lo | ((uint32_t)hi << 16);
+                            make_float2(y2, y3), __NV_SATFINITE, __NV_E4M3);
+                        w[e] = (uint32_t)lo | ((uint32_t)hi << 16);
                     }
-                    *reinterpret_cast<uint4 *>(a0 + swz(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(a0 + swz64(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             } else {
-                uint8_t *a1 = a0 + kTile;
+                uint8_t *a1 = a0 + kATile;
+                // 2 chunks of 8 values (16 values) per thread from the staged box
 #pragma unroll
-                for (int ac = 0; ac < 8; ++ac) {
-                    const uint8_t *xb = st + (ac >> 2) * kTile;
-                    const int c0 = (ac & 3) * 2;
-                    const float4 x0 = *reinterpret_cast<const float4 *>(xb + swz(r, c0));
-                    const float4 x1 = *reinterpret_cast<const float4 *>(xb + swz(r, c0 + 1));
+                for (int i = 0; i < 2; ++i) {
+                    const int ac = 2 * h + i;  // operand chunk: values ac*8 .. ac*8+7
+                    const float4 x0 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac));
+                    const float4 x1 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac + 1));
                     const float4 m0 = *reinterpret_cast<const float4 *>(mk + ac * 8);
                     const float4 m1 = *reinterpret_cast<const float4 *>(mk + ac * 8 + 4);
-                    float y[8] = {x0.x - m0.x, x0.y - m0.y, x0.z - m0.z, x0.w - m0.w,
-                                  x1.x - m1.x, x1.y - m1.y, x1.z - m1.z, x1.w - m1.w};
+                    float y[8] = {fmaf(x0.x, x_scale, m0.x), fmaf(x0.y, x_scale, m0.y),
+                                  fmaf(x0.z, x_scale, m0.z), fmaf(x0.w, x_scale, m0.w),
+                                  fmaf(x1.x, x_scale, m1.x), fmaf(x1.y, x_scale, m1.y),
+                                  fmaf(x1.z, x_scale, m1.z), fmaf(x1.w, x_scale, m1.w)};
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) nrm = fmaf(y[i], y[i], nrm);
+                    for (int e = 0; e < 8; ++e) nrm = fmaf(y[e], y[e], nrm);
                     if (MODE == kBF16) {
                         uint32_t w[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            w[i] = pack_b2(__floats2bfloat162_rn(y[2 * i], y[2 * i + 1]));
-                        *reinterpret_cast<uint4 *>(a0 + swz(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
+                        for (int e = 0; e < 4; ++e)
+                            w[e] = pack_b2(__floats2bfloat162_rn(y[2 * e], y[2 * e + 1]));
+                        *reinterpret_cast<uint4 *>(a0 + swz64(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
                     } else {
                         uint32_t wh[4], wl[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float s0 = y[2 * i] * x_scale, s1 = y[2 * i + 1] * x_scale;
-                            const __half2 h = __floats2half2_rn(s0, s1);
-                            const float2 hf = __half22float2(h);
-                            wh[i] = pack_h2(h);
-                            wl[i] = pack_h2(__floats2half2_rn(s0 - hf.x, s1 - hf.y));
+                        for (int e = 0; e < 4; ++e) {
+                            const __half2 hh = __floats2half2_rn(y[2 * e], y[2 * e + 1]);
+                            const float2 hf = __half22float2(hh);
+                            wh[e] = pack_h2(hh);
+                            wl[e] = pack_h2(__floats2half2_rn(y[2 * e] - hf.x, y[2 * e + 1] - hf.y));
                         }
-                        *reinterpret_cast<uint4 *>(a0 + swz(r, ac)) =
+                        *reinterpret_cast<uint4 *>(a0 + swz64(r, ac)) =
                             make_uint4(wh[0], wh[1], wh[2], wh[3]);
-                        *reinterpret_cast<uint4 *>(a1 + swz(r, ac)) =
+                        *reinterpret_cast<uint4 *>(a1 + swz64(r, ac)) =
                             make_uint4(wl[0], wl[1], wl[2], wl[3]);
                     }
                 }
@@ -374,7 +400,12 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv[s]);
         }
-        // ---- epilogue: accumulator row r -> O
+        // |x - c|^2 of the row: the two halves meet in shared memory
+        if (h == 1) nrm_half[r] = nrm;
+        named_sync(1, 32 * kConvWarps);
+        if (h == 0 && pass == 0 && row_ok && norms && ok)
+            norms[(row0 + r) * nstride] = (nrm + nrm_half[r]) / (x_scale * x_scale);
+        // ---- epilogue: accumulator row r, columns [h * np/2, (h+1) * np/2)
         int ready = 0;
         if (ok && lane == 0) ready = mbar_wait(accf, 0, abort_flag, err, 4) ? 1 : 0;
         ready = __shfl_sync(0xffffffffu, ready, 0);
@@ -383,28 +414,24 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
             float *orow = O + (row0 + r) * ldo;
             // interleaved: column `col` of row R at ((R / 32) * dk + col) * 32 + R % 32
             float *ogrp = O + (((row0 + r) >> 5) * (int64_t)dk << 5) + lane;
-            const bool vec = ((ldo & 3) == 0) && ((((uintptr_t)O) & 15) == 0);
+            const int half = np >> 1;  // a multiple of 8
+            const int cbeg = h * half, cend = cbeg + half;
 #pragma unroll 1
-            for (int c = 0; c < kNP; c += 16) {
+            for (int c = cbeg & ~15; c < cend; c += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-                const int col = col0 + c;
-                if (!row_ok || col >= dk) continue;
+                if (!row_ok) continue;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] *= col_scale[col + i];
-                if (il) {
-                    for (int i = 0; i < 16 && col + i < dk; ++i) ogrp[(int64_t)(col + i) << 5] = v[i];
-                } else if (vec && col + 16 <= dk) {
-#pragma unroll
-                    for (int i = 0; i < 16; i += 4)
-                        *reinterpret_cast<float4 *>(orow + col + i) =
-                            make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                } else {
-                    for (int i = 0; i < 16 && col + i < dk; ++i) orow[col + i] = v[i];
+                for (int i = 0; i < 16; ++i) {
+                    const int cc = c + i;
+                    const int col = col0 + cc;
+                    if (cc < cbeg || cc >= cend || col >= dk) continue;
+                    const float val = v[i] * col_scale[col];
+                    if (il) ogrp[(int64_t)col << 5] = val;
+                    else orow[col] = val;
                 }
             }
         }
-        if (pass == 0 && row_ok && norms) norms[(row0 + r) * nstride] = nrm;
         tc_fence_before();
     }
     __syncthreads();
@@ -442,7 +469,8 @@ saq_status get_encoder(PFN_cuTensorMapEncodeTiled_v12000 *fn) {
 }
 
 saq_status make_map(CUtensorMap *map, CUtensorMapDataType type, int elem, const void *ptr,
-                    uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer) {
+                    uint64_t inner, uint64_t outer, uint32_t box_inner, uint32_t box_outer,
+                    CUtensorMapSwizzle swz) {
     PFN_cuTensorMapEncodeTiled_v12000 enc;
     saq_status st = get_encoder(&enc);
     if (st != SAQ_OK) return st;
@@ -451,16 +479,17 @@ saq_status make_map(CUtensorMap *map, CUtensorMapDataType type, int elem, const 
     const cuuint32_t box[2] = {box_inner, box_outer};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = enc(map, type, 2, const_cast<void *>(ptr), dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(SAQ_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return SAQ_OK;
 }
 
 struct TcExtra {
     CUtensorMap b0, b1;
-    float *mean_pad = nullptr;
+    float *mcs = nullptr;  // -c * x_scale, padded to the K blocks
     float x_scale = 1.f;
+    int np = 0, npass = 0;
     int *err = nullptr;
 };
 
@@ -472,18 +501,18 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
     const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
     CUtensorMap tmx;
     saq_status st = make_map(&tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, (uint64_t)m->d,
-                             (uint64_t)n, 32, kBM);
+                             (uint64_t)n, 32, kBM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (st != SAQ_OK) return st;
-    const int npass = (m->dk + kNP - 1) / kNP;
-    const int nkb = (m->d + Cfg<MODE>::BK - 1) / Cfg<MODE>::BK;
+    const int nkb = m->tc.d_pad / Cfg<MODE>::BK;
+    const uint32_t sm = smem_bytes<MODE>(m->tc.d_pad);
     SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem_bytes<MODE>()));
+                                        (int)sm));
     const int64_t tiles = (n + kBM - 1) / kBM;
-    const int64_t blocks = tiles * npass;
+    const int64_t blocks = tiles * ex->npass;
     if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
-    k_proj_tc<MODE><<<(unsigned)blocks, kThreads, smem_bytes<MODE>(), s>>>(
-        tmx, ex->b0, ex->b1, n, m->dk, npass, nkb, ex->mean_pad, ex->x_scale, m->tc.col_scale, O,
-        ldo, layout == kInterleaved ? 1 : 0, norms, ns, ex->err);
+    k_proj_tc<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(
+        tmx, ex->b0, ex->b1, n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
+        m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, ex->err);
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
@@ -491,12 +520,14 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
 
 }  // namespace
 
-bool tc_supported(const saq_model *m) { return m->d % 4 == 0 && m->dk > 0; }
+// d % 4 == 0 for the FP32 tensor map; the -c*s copy of the K range must fit
+// in shared memory next to the stages.
+bool tc_supported(const saq_model *m) { return m->d % 4 == 0 && m->dk > 0 && m->d <= 6144; }
 
 void tc_release(saq_model *m) {
     TcExtra *ex = static_cast<TcExtra *>(m->tc.extra);
     if (ex) {
-        cudaFree(ex->mean_pad);
+        cudaFree(ex->mcs);
         cudaFree(ex->err);
         delete ex;
     }
@@ -506,16 +537,19 @@ void tc_release(saq_model *m) {
     m->tc = TcOperands{};
 }
 
-// Device operands of W for `precision`: zero-padded to dk_pad x d_pad, plus
-// the per-column dequantisation scale and the padded mean.
+// Device operands of W for `precision`: zero-padded to dk_pad x d_pad, the
+// per-column dequantisation scale, and -c * x_scale for the centring FMA.
 saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     if (!tc_supported(m))
-        return set_error(SAQ_ERR_UNSUPPORTED, "tensor-core projection needs d %% 4 == 0");
+        return set_error(SAQ_ERR_UNSUPPORTED, "tensor-core projection needs d %% 4 == 0, d <= 6144");
     tc_release(m);
-    const int BK = precision == SAQ_PREC_FP8 ? 128 : 64;
+    const int BK = precision == SAQ_PREC_FP8 ? 64 : 32;
     const int dpad = (m->d + BK - 1) / BK * BK;
-    const int dkpad = (m->dk + kNP - 1) / kNP * kNP;
     const int d = m->d, dk = m->dk;
+    // balanced column passes of at most 256 columns, multiples of 16
+    const int npass = (dk + kNPMax - 1) / kNPMax;
+    const int np = ((dk + npass - 1) / npass + 15) / 16 * 16;
+    const int dkpad = npass * np;
     // input scale from the fitted variances (a power of two: exact)
     double tot = 0;
     for (double v : m->sig2) tot += v;
@@ -527,6 +561,8 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     m->tc.precision = precision;
     m->tc.dk_pad = dkpad;
     m->tc.d_pad = dpad;
+    ex->np = np;
+    ex->npass = npass;
     if (precision == SAQ_PREC_FP32) {
         xs = rms > 0 ? pow2_near(8.0 / rms) : 1.0;
         ws = 1024.0;
@@ -577,11 +613,11 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     SAQ_CUDA_CHECK(cudaMalloc(&m->tc.col_scale, sizeof(float) * cs.size()));
     SAQ_CUDA_CHECK(cudaMemcpy(m->tc.col_scale, cs.data(), sizeof(float) * cs.size(),
                               cudaMemcpyHostToDevice));
+    // -c * s, exact (s is a power of two); y = fma(x, s, -c*s) = round((x - c) s)
     std::vector<float> mp((size_t)dpad, 0.f);
-    for (int k = 0; k < d; ++k) mp[(size_t)k] = (float)m->mean[(size_t)k];
-    SAQ_CUDA_CHECK(cudaMalloc(&ex->mean_pad, sizeof(float) * mp.size()));
-    SAQ_CUDA_CHECK(cudaMemcpy(ex->mean_pad, mp.data(), sizeof(float) * mp.size(),
-                              cudaMemcpyHostToDevice));
+    for (int k = 0; k < d; ++k) mp[(size_t)k] = -(float)m->mean[(size_t)k] * (float)xs;
+    SAQ_CUDA_CHECK(cudaMalloc(&ex->mcs, sizeof(float) * mp.size()));
+    SAQ_CUDA_CHECK(cudaMemcpy(ex->mcs, mp.data(), sizeof(float) * mp.size(), cudaMemcpyHostToDevice));
     SAQ_CUDA_CHECK(cudaMalloc(&ex->err, sizeof(int)));
     SAQ_CUDA_CHECK(cudaMemset(ex->err, 0, sizeof(int)));
     const bool f8 = precision == SAQ_PREC_FP8;
@@ -590,12 +626,12 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
                                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
     const int es = f8 ? 1 : 2;
     saq_status st = make_map(&ex->b0, t, es, m->tc.w_hi, (uint64_t)dpad, (uint64_t)dkpad,
-                             (uint32_t)BK, kNP);
+                             (uint32_t)BK, (uint32_t)np, CU_TENSOR_MAP_SWIZZLE_64B);
     if (st != SAQ_OK) return st;
     ex->b1 = ex->b0;
     if (m->tc.w_lo) {
         st = make_map(&ex->b1, t, es, m->tc.w_lo, (uint64_t)dpad, (uint64_t)dkpad, (uint32_t)BK,
-                      kNP);
+                      (uint32_t)np, CU_TENSOR_MAP_SWIZZLE_64B);
         if (st != SAQ_OK) return st;
     }
     return SAQ_OK;
