@@ -232,13 +232,14 @@ def run_ours(args):
     t_max = max_over_ranks(world, t_dev)
     value = n * world * args.steps / t_max
 
-    # per-kernel breakdown of one step: projection alone and quantization alone
-    O_buf, nrm = m.project(X[:min(n, 262144)])
-    rows = O_buf.shape[0]
-    t_proj = time_events(lambda: m.project(X[:rows]), 3, stream) * n / rows
-    Oc = O_buf.contiguous()
-    t_caq = time_events(lambda: m.quantize_projected(Oc, nrm), 3, stream) * n / rows
-    del O_buf, Oc
+    # per-kernel breakdown of one step, in the encode's own data layout:
+    # projection alone and quantize/adjust/pack alone (serial, no overlap)
+    rows = min(n, 262144)
+    O_buf, nrm = m.project_interleaved(X[:rows])
+    c2, f2 = m.alloc_outputs(rows, dev)
+    t_proj = time_events(lambda: m.project_interleaved(X[:rows]), 3, stream) * n / rows
+    t_caq = time_events(lambda: m.quantize_interleaved(O_buf, nrm, c2, f2), 3, stream) * n / rows
+    del O_buf, c2, f2
     plan = m.plan
     dk = m.d_kept
     flops = 2.0 * n * d * dk

@@ -178,6 +178,18 @@ saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
                                   const float *norms2_dev, int64_t n,
                                   uint8_t *codes_dev, float *factors_dev,
                                   void *stream);
+/* The same with a layout flag: interleaved != 0 selects the layout the
+ * encode uses internally, rows in groups of 32:
+ *   O_dev[((i / 32) * d_kept + j) * 32 + i % 32] = o_i[j],
+ * with room for ceil(n / 32) * 32 rows.  interleaved == 0 is the row-major
+ * layout of saq_project / saq_quantize_projected. */
+saq_status saq_project_ex(const saq_model *m, const float *X_dev, int64_t n,
+                          float *O_dev, float *norms2_dev, int32_t interleaved,
+                          void *stream);
+saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
+                                     const float *norms2_dev, int64_t n,
+                                     uint8_t *codes_dev, float *factors_dev,
+                                     int32_t interleaved, void *stream);
 
 /*
  * saq_encode for callers that cannot allocate device memory.  The paper has

@@ -35,7 +35,7 @@ EXPORTS = [
     "saq_status_string", "saq_plan_search", "saq_kernel_launch_count",
     "saq_encode_noalloc", "saq_model_uses_tensor_cores", "saq_check_device",
     "saq_ingest_open", "saq_ingest_submit", "saq_ingest_poll", "saq_ingest_wait",
-    "saq_ingest_get_stats", "saq_ingest_close",
+    "saq_ingest_get_stats", "saq_ingest_close", "saq_project_ex", "saq_quantize_projected_ex",
 ]
 
 
@@ -117,6 +117,8 @@ def load() -> ctypes.CDLL:
         "saq_ingest_wait": (st, [vp, ctypes.c_uint64, i32, ctypes.POINTER(ctypes.c_double)]),
         "saq_ingest_get_stats": (st, [vp, ctypes.POINTER(saq_ingest_stats)]),
         "saq_ingest_close": (st, [vp]),
+        "saq_project_ex": (st, [mp, vp, i64, vp, vp, i32, vp]),
+        "saq_quantize_projected_ex": (st, [mp, vp, vp, i64, vp, vp, i32, vp]),
         "saq_plan_search": (st, [dp, i32, i32, i64, i32, ctypes.c_double,
                                  ctypes.POINTER(saq_segment), i32, ctypes.POINTER(i32), dp]),
     }
@@ -271,6 +273,25 @@ class Model:
         codes, factors = self.alloc_outputs(n, O.device)
         _check(load().saq_quantize_projected(self._h, _dptr(O), _dptr(norms2), n, _dptr(codes),
                                              _dptr(factors), _stream(stream)))
+        return codes[:, :self.code_bytes], factors
+
+    def project_interleaved(self, X: torch.Tensor, stream=None):
+        """Projection into the encode's internal layout (groups of 32 rows)."""
+        n = X.shape[0]
+        O = torch.empty(((n + 31) // 32 * 32 * max(self.d_kept, 1),), dtype=torch.float32,
+                        device=X.device)
+        nrm = torch.empty((n,), dtype=torch.float32, device=X.device)
+        _check(load().saq_project_ex(self._h, _dptr(X), n, _dptr(O), _dptr(nrm), 1,
+                                     _stream(stream)))
+        return O, nrm
+
+    def quantize_interleaved(self, Oi: torch.Tensor, norms2: torch.Tensor, codes=None,
+                             factors=None, stream=None):
+        n = norms2.shape[0]
+        if codes is None:
+            codes, factors = self.alloc_outputs(n, Oi.device)
+        _check(load().saq_quantize_projected_ex(self._h, _dptr(Oi), _dptr(norms2), n,
+                                                _dptr(codes), _dptr(factors), 1, _stream(stream)))
         return codes[:, :self.code_bytes], factors
 
     def estimate_dist(self, codes: torch.Tensor, factors: torch.Tensor, Q: torch.Tensor,

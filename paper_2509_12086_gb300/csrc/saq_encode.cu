@@ -74,6 +74,57 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
     return SAQ_OK;
 }
 
+// Chunked encode with the projection of chunk i + 1 (tensor cores) running
+// on one library stream while chunk i is quantized (CUDA cores) on another;
+// two scratch buffers alternate.  Forks from and joins back into `s`.
+saq_status encode_rows_overlapped(saq_model *m, const float *X, int64_t n, uint8_t *codes,
+                                  float *factors, void *scratch0, void *scratch1, int64_t rows,
+                                  cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(m->pipe_mu);
+    if (!m->pipe_s[0]) {
+        // the projection stream gets the higher priority: its CTAs (tensor
+        // cores, few issue slots) are placed first, the quantize blocks fill
+        // the remaining issue capacity
+        int lo = 0, hi = 0;
+        SAQ_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        for (int i = 0; i < 2; ++i) {
+            SAQ_CUDA_CHECK(cudaStreamCreateWithPriority(&m->pipe_s[i], cudaStreamNonBlocking,
+                                                        i == 0 ? hi : lo));
+            SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_proj[i], cudaEventDisableTiming));
+            SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_caq[i], cudaEventDisableTiming));
+            SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_join[i], cudaEventDisableTiming));
+        }
+        SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+    }
+    cudaStream_t ps = m->pipe_s[0], qs = m->pipe_s[1];
+    SAQ_CUDA_CHECK(cudaEventRecord(m->ev_fork, s));
+    SAQ_CUDA_CHECK(cudaStreamWaitEvent(ps, m->ev_fork, 0));
+    SAQ_CUDA_CHECK(cudaStreamWaitEvent(qs, m->ev_fork, 0));
+    saq_status st = SAQ_OK;
+    int64_t i = 0;
+    for (int64_t r0 = 0; r0 < n && st == SAQ_OK; r0 += rows, ++i) {
+        const int b = (int)(i & 1);
+        void *scr = b ? scratch1 : scratch0;
+        const int64_t nr = std::min(rows, n - r0);
+        if (i >= 2) SAQ_CUDA_CHECK(cudaStreamWaitEvent(ps, m->ev_caq[b], 0));
+        st = project_rows(m, X + r0 * m->d, nr, static_cast<float *>(scr), m->dk, kInterleaved,
+                          factors + r0 * m->nf, m->nf, ps);
+        if (st != SAQ_OK) break;
+        SAQ_CUDA_CHECK(cudaEventRecord(m->ev_proj[b], ps));
+        SAQ_CUDA_CHECK(cudaStreamWaitEvent(qs, m->ev_proj[b], 0));
+        st = quantize_rows(m, scr, rows, nr, codes + r0 * (int64_t)m->code_bytes,
+                           factors + r0 * m->nf, qs);
+        if (st != SAQ_OK) break;
+        SAQ_CUDA_CHECK(cudaEventRecord(m->ev_caq[b], qs));
+    }
+    // join both streams back into the caller's stream (also on failure)
+    cudaEventRecord(m->ev_join[0], ps);
+    cudaEventRecord(m->ev_join[1], qs);
+    cudaStreamWaitEvent(s, m->ev_join[0], 0);
+    cudaStreamWaitEvent(s, m->ev_join[1], 0);
+    return st;
+}
+
 }  // namespace saq
 
 using namespace saq;
@@ -94,12 +145,19 @@ saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n, uint8_t
     if (st != SAQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (m->dk == 0) return launch_rownorm2(m, X_dev, n, factors_dev, m->nf, s);
-    const int64_t rows = chunk_rows(m, n, (size_t)512 << 20);
+    // chunks of projected rows of about 256 MB; with more than one chunk the
+    // projection of the next chunk overlaps the quantization of this one
+    const int64_t rows = chunk_rows(m, n, (size_t)256 << 20);
+    const int nbuf = rows < n ? 2 : 1;
+    const size_t sb = encode_scratch_bytes(m, rows);
     void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, encode_scratch_bytes(m, rows), s);
+    cudaError_t e = cudaMallocAsync(&scratch, sb * (size_t)nbuf, s);
     if (e != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
-    st = encode_rows(m, X_dev, n, codes_dev, factors_dev, scratch, rows, s);
+    if (nbuf == 1) st = encode_rows(m, X_dev, n, codes_dev, factors_dev, scratch, rows, s);
+    else
+        st = encode_rows_overlapped(const_cast<saq_model *>(m), X_dev, n, codes_dev, factors_dev,
+                                    scratch, static_cast<uint8_t *>(scratch) + sb, rows, s);
     cudaFreeAsync(scratch, s);
     return st;
 }
@@ -118,6 +176,50 @@ saq_status saq_project(const saq_model *m, const float *X_dev, int64_t n, float 
     if (st != SAQ_OK) return st;
     return project_rows(m, X_dev, n, O_dev, m->dk, kRowMajor, norms2_dev, 1,
                         (cudaStream_t)stream);
+}
+
+saq_status saq_project_ex(const saq_model *m, const float *X_dev, int64_t n, float *O_dev,
+                          float *norms2_dev, int32_t interleaved, void *stream) {
+    clear_error();
+    if (!interleaved) return saq_project(m, X_dev, n, O_dev, norms2_dev, stream);
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0) return set_error(SAQ_ERR_INVALID, "n < 0");
+    if (n == 0) return SAQ_OK;
+    if (!X_dev || !norms2_dev || (m->dk > 0 && !O_dev))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(X_dev) || !aligned16(O_dev) || !aligned16(norms2_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    return project_rows(m, X_dev, n, O_dev, m->dk, kInterleaved, norms2_dev, 1,
+                        (cudaStream_t)stream);
+}
+
+saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
+                                     const float *norms2_dev, int64_t n, uint8_t *codes_dev,
+                                     float *factors_dev, int32_t interleaved, void *stream) {
+    clear_error();
+    if (!interleaved)
+        return saq_quantize_projected(m, O_dev, norms2_dev, n, codes_dev, factors_dev, stream);
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0) return set_error(SAQ_ERR_INVALID, "n < 0");
+    if (n == 0) return SAQ_OK;
+    if (!norms2_dev || !factors_dev || (m->dk > 0 && (!O_dev || !codes_dev)))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(O_dev) || !aligned16(codes_dev) || !aligned16(factors_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = launch_copy_strided(norms2_dev, 1, factors_dev, m->nf, n, s);
+    if (st != SAQ_OK || m->dk == 0) return st;
+    uint8_t *cs = nullptr;
+    const size_t cb = (size_t)((n + 31) / 32 * 32) * (size_t)m->dk;
+    if (cudaMallocAsync((void **)&cs, cb, s) != cudaSuccess)
+        return set_error(SAQ_ERR_OOM, "scratch allocation failed");
+    st = launch_caq1(m, O_dev, n, cs, codes_dev, factors_dev, s);
+    cudaFreeAsync(cs, s);
+    return st;
 }
 
 saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,

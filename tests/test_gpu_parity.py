@@ -304,3 +304,17 @@ def test_precision_forms_error_bounded(c1, prec):
     rg = O.relative_error(dg.astype(np.float64), ex).mean()
     ro = O.relative_error(O.estimate(mo, eo.codes, eo.factors, Qm), ex).mean()
     assert rg <= (2.0 if prec == "bf16" else 4.0) * ro + 1e-4, (rg, ro)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_simt"])
+def test_interleaved_halves_equal_encode(c1, prec):
+    """saq_project_ex + saq_quantize_projected_ex in the encode's own layout
+    (rows in groups of 32) reproduce saq_encode bit for bit, including a
+    ragged last group."""
+    X, Qm, mo, eo = c1
+    m = lib_model(mo, prec)
+    Xd = torch.from_numpy(X[:9999]).cuda()
+    ref_c, ref_f = m.encode(Xd)
+    Oi, nrm = m.project_interleaved(Xd)
+    c, f = m.quantize_interleaved(Oi, nrm)
+    assert torch.equal(c, ref_c) and torch.equal(f, ref_f)
