@@ -118,13 +118,19 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, x):
+def max_over_ranks(world, x, device="cuda"):
+    """Slowest rank's time: the whole job ends when the last replica ends."""
     if world <= 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Each rank encodes its own batch (weak scaling); seeds differ by rank."""
+    return synth.SEED_DATA + 7919 * rank
 
 
 def workload_desc(w, name, precision, plan, code_bytes):
@@ -209,7 +215,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     # each rank encodes its own batch (weak scaling, no collective on the data path)
-    X = synth.power_law(n, d, w["alpha"], seed=synth.SEED_DATA + 7919 * rank, device=dev)
+    X = synth.power_law(n, d, w["alpha"], seed=replica_seed(rank), device=dev)
     m = P.saq_fit(X, avg_bits=w["avg_bits"], rounds=w["rounds"], precision=args.precision)
     codes, factors = m.alloc_outputs(n, dev)
 
@@ -286,6 +292,23 @@ def run_ours(args):
                "rows_per_step": ne}
         del Xh, ch, fh
 
+    # the precision forms on the same batch (BF16 / FP8 projection, FP32 quantization)
+    forms = {}
+    if not args.no_forms:
+        for prec in ("bf16", "fp8"):
+            m.set_precision(prec)
+            for _ in range(2):
+                step()
+            t = time_events(step, max(3, args.steps // 2), stream)
+            forms[prec] = {"value": n * world / t, "unit": UNIT, "ms_per_step": t * 1e3,
+                           "tensor_cores": m.tensor_cores}
+        m.set_precision(args.precision)
+
+    # serving form: Poisson stream of insert requests over three collections
+    ingest = None
+    if not args.no_ingest and rank == 0:
+        ingest = serving_run(args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = cpu_baseline(w, X)
@@ -304,11 +327,73 @@ def run_ours(args):
                "step_roofline_vectors_per_s": step_roof,
                "step_roofline_frac": value / world / step_roof,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-               "clocks": clocks}
+               "clocks": clocks, "precision_forms": forms, "ingest": ingest}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serving_run(args, dev):
+    """Continuous-batching ingest (include/saq.h saq_ingest_*): three resident
+    collections (d = 128 / 960 at 4 b/dim, d = 1536 at 2 b/dim, alpha 0.8),
+    requests of log-uniform size in [1, 65536] rows, Poisson arrivals at a
+    load factor of the measured capacity, HBM budget 40 GB."""
+    rng = np.random.default_rng(2024)
+    specs = [(128, 4.0), (960, 4.0), (1536, 2.0)]
+    models = []
+    for d, bits in specs:
+        Xf = synth.power_law(100_000, d, 0.8, seed=17 + d, device=dev)
+        models.append(P.saq_fit(Xf, avg_bits=bits))
+    # capacity of each collection (vectors/s) from a warm encode of 131,072 rows
+    cap = []
+    for (d, _), mm in zip(specs, models):
+        Xc = synth.power_law(131_072, d, 0.8, seed=99 + d, device=dev)
+        c, f = mm.alloc_outputs(Xc.shape[0], dev)
+        mm.encode(Xc, c, f)
+        t = time_events(lambda: mm.encode(Xc, c, f), 3, torch.cuda.current_stream(dev))
+        cap.append(Xc.shape[0] / t)
+        del Xc, c, f
+    total = args.ingest_vectors
+    sizes, colls = [], []
+    while sum(sizes) < total:
+        sizes.append(int(np.exp(rng.uniform(0.0, np.log(65536.0)))))
+        colls.append(int(rng.integers(0, 3)))
+    # time per vector of the mix; arrivals at load factor rho of that capacity
+    sec_per_vec = np.mean([1.0 / cap[c] for c in colls])
+    rate = args.ingest_load / (sec_per_vec * np.mean(sizes))  # requests / s
+    gaps = rng.exponential(1.0 / rate, size=len(sizes))
+    # request rows in page-locked host memory (generated on the GPU)
+    reqs = []
+    for i, (nr, c) in enumerate(zip(sizes, colls)):
+        Xr = synth.power_law(nr, specs[c][0], 0.8, seed=5000 + i, device=dev).cpu().pin_memory()
+        m = models[c]
+        cb = torch.empty((nr, max(m.code_bytes, 1)), dtype=torch.uint8).pin_memory()
+        fb = torch.empty((nr, m.factor_count), dtype=torch.float32).pin_memory()
+        reqs.append((c, Xr, cb, fb))
+    svc = P.Ingest(models, hbm_budget_bytes=40 << 30, max_batch_rows=65536, slots=4)
+    tickets = []
+    t0 = time.perf_counter()
+    due = t0
+    for (c, Xr, cb, fb), g in zip(reqs, gaps):
+        due += g
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        tickets.append(svc.submit(c, Xr, cb, fb))
+    lats = [svc.wait(t, timeout_ms=120000)[2] for t in tickets]
+    wall = time.perf_counter() - t0
+    st = svc.stats()
+    svc.close()
+    lat = np.array(lats)
+    return {"requests": len(sizes), "vectors": int(sum(sizes)),
+            "load_factor": args.ingest_load, "arrival_rate_per_s": rate,
+            "capacity_vectors_per_s": {str(d): v for (d, _), v in zip(specs, cap)},
+            "vectors_per_s": sum(sizes) / wall, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3), "batches": int(st["batches"]),
+            "slots": 4, "max_batch_rows": 65536, "hbm_budget_gb": 40,
+            "collections": "d128@4b, d960@4b, d1536@2b (alpha 0.8)"}
 
 
 def tc_enabled(m):
@@ -331,6 +416,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-ingest", action="store_true")
+    ap.add_argument("--ingest-vectors", type=int, default=2_000_000)
+    ap.add_argument("--ingest-load", type=float, default=0.8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

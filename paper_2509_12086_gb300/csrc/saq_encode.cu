@@ -82,14 +82,8 @@ saq_status encode_rows_overlapped(saq_model *m, const float *X, int64_t n, uint8
                                   cudaStream_t s) {
     std::lock_guard<std::mutex> lk(m->pipe_mu);
     if (!m->pipe_s[0]) {
-        // the projection stream gets the higher priority: its CTAs (tensor
-        // cores, few issue slots) are placed first, the quantize blocks fill
-        // the remaining issue capacity
-        int lo = 0, hi = 0;
-        SAQ_CUDA_CHECK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         for (int i = 0; i < 2; ++i) {
-            SAQ_CUDA_CHECK(cudaStreamCreateWithPriority(&m->pipe_s[i], cudaStreamNonBlocking,
-                                                        i == 0 ? hi : lo));
+            SAQ_CUDA_CHECK(cudaStreamCreateWithFlags(&m->pipe_s[i], cudaStreamNonBlocking));
             SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_proj[i], cudaEventDisableTiming));
             SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_caq[i], cudaEventDisableTiming));
             SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_join[i], cudaEventDisableTiming));
