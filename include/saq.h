@@ -202,13 +202,15 @@ saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
  * synchronise the device; or a host (a database extension, a plugin) that
  * forbids driver allocations from inside its callbacks.  This entry point
  * allocates nothing: its scratch (the projected rows, 4 bytes per row and kept
- * dimension, and their codes during adjustment, 1 byte) lives in a fixed
- * 32 MiB array in the library's device memory, which every GPU that loads
- * the library keeps until the process exits.
+ * dimension, their codes during adjustment, 1 byte, and the largest
+ * magnitude per row and kept segment, 4 bytes) lives in a fixed 32 MiB array
+ * in the library's device memory, which every GPU that loads the library
+ * keeps until the process exits.
  *
- * Limit: ceil(n / 32) * 32 * d_kept * 5 bytes <= 32 MiB, e.g. 6,976 rows at
- * d_kept = 960; larger n is rejected with SAQ_ERR_INVALID before any launch
- * (the message states the largest n for the model).  Arguments and outputs
+ * Limit: ceil(n / 32) * 32 * (5 * d_kept + 4 * segments) bytes <= 32 MiB,
+ * e.g. 6,944 rows at d_kept = 960 in 4 kept segments; larger n is rejected
+ * with SAQ_ERR_INVALID before any launch (the message states the largest n
+ * for the model).  Arguments and outputs
  * are as for saq_encode.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any

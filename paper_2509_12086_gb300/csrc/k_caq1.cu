@@ -17,8 +17,10 @@
 // At most one of the two moves can raise the cosine (the superlevel set of the
 // cosine is a convex cone), and the paper's -Delta trial after an accepted
 // +Delta returns to the old point and is rejected.  A lane whose round made no
-// move stops (its state no longer changes).  I and S are recomputed exactly
-// for the stored factors.
+// move stops (its state no longer changes).  v_max comes from the projection
+// (or a separate pass), so the rows are streamed once for the initial codes
+// and once per round; S is tracked exactly as an integer, I in FP32, and the
+// bit-planes are packed from the codes alone.
 #include <algorithm>
 
 #include "saq_internal.h"
@@ -39,22 +41,16 @@ struct SegTable {
     int order[kMaxSeg];  // segments by decreasing length: long work starts first
 };
 
-// Bit-planes of one lane's segment (most significant first, 64-bit words)
-// and the exact factors.
+// Bit-planes of one lane's segment from its codes (most significant first,
+// 64-bit words).
 template <int B>
-__device__ __forceinline__ void pack_segment(const float *op, const uint8_t *cp, int len,
-                                             bool valid, uint64_t *cout, int words, float &If,
-                                             int &Si) {
-    constexpr int cmax = (1 << B) - 1;
+__device__ __forceinline__ void pack_segment(const uint8_t *cp, int len, bool valid,
+                                             uint64_t *cout, int words) {
     uint64_t w[B];
 #pragma unroll
     for (int p = 0; p < B; ++p) w[p] = 0ull;
     for (int j = 0; j < len; ++j) {
-        const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
         const int c = cp[(int64_t)j << 5];
-        const int u = 2 * c - cmax;
-        If = fmaf((float)u, x, If);
-        Si += u * u;
         const int bp = j & 63;
 #pragma unroll
         for (int p = 0; p < B; ++p) w[p] |= (uint64_t)((c >> (B - 1 - p)) & 1) << bp;
@@ -73,13 +69,14 @@ __device__ __forceinline__ void pack_segment(const float *op, const uint8_t *cp,
 // chunk in one launch.
 __global__ void __launch_bounds__(256)
 k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable t, int rounds,
-       uint8_t *__restrict__ cs, uint8_t *__restrict__ codes, int64_t code_stride,
-       float *__restrict__ factors, int nf) {
+       uint8_t *__restrict__ cs, const float *__restrict__ vmax_arr,
+       uint8_t *__restrict__ codes, int64_t code_stride, float *__restrict__ factors, int nf) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t groups = (n + 31) / 32;
     if (w >= groups * nseg) return;  // uniform per warp
-    const Seg sg = t.s[t.order[w / groups]];
+    const int si = t.order[w / groups];
+    const Seg sg = t.s[si];
     const int64_t g = w % groups;
     const int off = sg.off, len = sg.len, B = sg.bits, words = sg.words, fidx = sg.fidx;
     const long long code_off = sg.code_off;
@@ -89,16 +86,13 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
     const float *op = Oi + ((g * dk + off) << 5) + lane;
     uint8_t *cp = cs + ((g * dk + off) << 5) + lane;
 
-    float vmax = 0.f, n2 = 0.f;
-    for (int j = 0; j < len; ++j) {
-        const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
-        vmax = fmaxf(vmax, fabsf(x));
-        n2 = fmaf(x, x, n2);
-    }
+    // v_max of the lane's vector-segment, recorded by the projection
+    const float vmax = valid ? __ldg(vmax_arr + ((g * nseg + si) << 5) + lane) : 0.f;
     const bool live = valid && vmax > 0.f;
-    // Eq. find_nearest_code: c = floor((o + v_max) / Delta), Delta = 2 v_max / 2^B
+    // initial codes, Eq. find_nearest_code: c = floor((o + v_max) / Delta),
+    // Delta = 2 v_max / 2^B; with I = <u, o>, S = |u|^2 and |o|^2
     const float inv_delta = live ? (float)(1 << (B - 1)) / vmax : 0.f;
-    float I = 0.f;
+    float I = 0.f, n2 = 0.f;
     int Si = 0;
     for (int j = 0; j < len; ++j) {
         const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
@@ -110,6 +104,7 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
         cp[(int64_t)j << 5] = (uint8_t)c;
         const int u = 2 * c - cmax;
         I = fmaf((float)u, x, I);
+        n2 = fmaf(x, x, n2);
         Si += u * u;
     }
     float Sf = (float)Si;
@@ -151,6 +146,8 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
                     const float sg = ap ? 1.f : -1.f;
                     I = fmaf(2.f * sg, x, I);
                     Sf += fmaf(4.f * sg, u, 4.f);
+                    const int ui = 2 * c - cmax;  // |u|^2 changes by 4su + 4, exactly
+                    Si += ap ? 4 * ui + 4 : 4 - 4 * ui;
                     rI = __fdividef(1.f, I);
                     alpha = Sf * rI;
                     beta = alpha * rI;
@@ -167,32 +164,49 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
         active = active && moved;
     }
 
-    // factors and bit-planes (most significant first, 64-bit little-endian words)
-    float If = 0.f;
-    Si = 0;
+    // bit-planes from the codes (most significant first, 64-bit words)
     uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
     switch (B) {  // uniform per warp
-        case 1: pack_segment<1>(op, cp, len, valid, cout, words, If, Si); break;
-        case 2: pack_segment<2>(op, cp, len, valid, cout, words, If, Si); break;
-        case 3: pack_segment<3>(op, cp, len, valid, cout, words, If, Si); break;
-        case 4: pack_segment<4>(op, cp, len, valid, cout, words, If, Si); break;
-        case 5: pack_segment<5>(op, cp, len, valid, cout, words, If, Si); break;
-        case 6: pack_segment<6>(op, cp, len, valid, cout, words, If, Si); break;
-        case 7: pack_segment<7>(op, cp, len, valid, cout, words, If, Si); break;
-        default: pack_segment<8>(op, cp, len, valid, cout, words, If, Si); break;
+        case 1: pack_segment<1>(cp, len, valid, cout, words); break;
+        case 2: pack_segment<2>(cp, len, valid, cout, words); break;
+        case 3: pack_segment<3>(cp, len, valid, cout, words); break;
+        case 4: pack_segment<4>(cp, len, valid, cout, words); break;
+        case 5: pack_segment<5>(cp, len, valid, cout, words); break;
+        case 6: pack_segment<6>(cp, len, valid, cout, words); break;
+        case 7: pack_segment<7>(cp, len, valid, cout, words); break;
+        default: pack_segment<8>(cp, len, valid, cout, words); break;
     }
     if (valid) {
         float *fo = factors + v * nf;
         if (live) {
             const float nrm = sqrtf(n2);
             fo[fidx] = nrm;
-            fo[fidx + 1] = If / (sqrtf((float)Si) * nrm);
+            fo[fidx + 1] = I / (sqrtf((float)Si) * nrm);
         } else {
             // all-zero segment (the paper is silent): codes 0, |o| = 0, cos = 1
             fo[fidx] = 0.f;
             fo[fidx + 1] = 1.f;
         }
     }
+}
+
+// v_max of every (row, kept segment) of interleaved rows: one warp per (group
+// of 32 rows, kept segment), lane = row.
+__global__ void __launch_bounds__(256)
+k_seg_vmax(const float *__restrict__ Oi, int64_t n, int dk, const SegCols sc,
+           float *__restrict__ vmax) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t groups = (n + 31) / 32;
+    if (w >= groups * sc.nk) return;
+    const int64_t g = w / sc.nk;
+    const int s = (int)(w % sc.nk);
+    const int c0 = s == 0 ? 0 : sc.end[s - 1], c1 = sc.end[s];
+    const bool valid = g * 32 + lane < n;
+    float mx = 0.f;
+    for (int c = c0; c < c1; ++c)
+        mx = fmaxf(mx, valid ? fabsf(__ldg(Oi + ((g * dk + c) << 5) + lane)) : 0.f);
+    vmax[((g * sc.nk + s) << 5) + lane] = mx;
 }
 
 // Row-major O (n x dk, ldo) -> interleaved O_i (groups of 32 rows).
@@ -217,7 +231,7 @@ __global__ void k_interleave(const float *__restrict__ O, int64_t ldo, int64_t n
 }  // namespace
 
 saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
-                       uint8_t *codes, float *factors, cudaStream_t s) {
+                       const float *vmax, uint8_t *codes, float *factors, cudaStream_t s) {
     const int nk = (int)m->kept.size();
     if (n <= 0 || nk == 0) return SAQ_OK;
     if (nk > kMaxSeg) return set_error(SAQ_ERR_UNSUPPORTED, "more than %d kept segments", kMaxSeg);
@@ -232,8 +246,19 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
     std::stable_sort(t.order, t.order + nk, [&](int a, int b) { return t.s[a].len > t.s[b].len; });
     const int64_t warps = (n + 31) / 32 * nk;
     const int64_t blocks = (warps + 7) / 8;
-    k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, m->dk, nk, t, m->rounds, cs, codes,
+    k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, m->dk, nk, t, m->rounds, cs, vmax, codes,
                                             (int64_t)m->code_bytes, factors, m->nf);
+    note_launches();
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return SAQ_OK;
+}
+
+saq_status launch_seg_vmax(const saq_model *m, const float *Oi, int64_t n, float *vmax,
+                           cudaStream_t s) {
+    const SegCols sc = seg_cols(m);
+    if (n <= 0 || sc.nk == 0) return SAQ_OK;
+    const int64_t warps = (n + 31) / 32 * sc.nk;
+    k_seg_vmax<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(Oi, n, m->dk, sc, vmax);
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;

@@ -217,7 +217,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
           const __grid_constant__ CUtensorMap tmb1, int64_t n, int dk, int npass, int np, int nkb,
           const float *__restrict__ mcs_g, float x_scale, const float *__restrict__ col_scale,
           float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms,
-          int64_t nstride, int *__restrict__ err) {
+          int64_t nstride, float *__restrict__ vmax, const SegCols segc,
+          int *__restrict__ err) {
     using C = Cfg<MODE>;
     constexpr uint32_t SB = stage_bytes<MODE>();
     extern __shared__ uint8_t smem_raw[];
@@ -416,6 +417,12 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
             float *ogrp = O + (((row0 + r) >> 5) * (int64_t)dk << 5) + lane;
             const int half = np >> 1;  // a multiple of 8
             const int cbeg = h * half, cend = cbeg + half;
+            // running max |o| of the current kept segment (interleaved layout only)
+            const bool want_vmax = il && vmax != nullptr;
+            float *vgrp = want_vmax ? vmax + (((row0 + r) >> 5) * (int64_t)segc.nk << 5) + lane
+                                    : nullptr;
+            int si = 0;
+            float mx = 0.f;
 #pragma unroll 1
             for (int c = cbeg & ~15; c < cend; c += 16) {
                 float v[16];
@@ -429,8 +436,18 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
                     const float val = v[i] * col_scale[col];
                     if (il) ogrp[(int64_t)col << 5] = val;
                     else orow[col] = val;
+                    if (want_vmax) {
+                        while (col >= segc.end[si]) {
+                            if (mx > 0.f) atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+                            mx = 0.f;
+                            ++si;
+                        }
+                        mx = fmaxf(mx, fabsf(val));
+                    }
                 }
             }
+            if (want_vmax && row_ok && mx > 0.f)
+                atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
         }
         tc_fence_before();
     }
@@ -497,7 +514,7 @@ double pow2_near(double x) { return ldexp(1.0, (int)lround(log2(x))); }
 
 template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, int64_t n,
                                            float *O, int64_t ldo, int layout, float *norms,
-                                           int64_t ns, cudaStream_t s) {
+                                           int64_t ns, float *vmax, cudaStream_t s) {
     const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
     CUtensorMap tmx;
     saq_status st = make_map(&tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, (uint64_t)m->d,
@@ -512,7 +529,8 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
     if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
     k_proj_tc<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(
         tmx, ex->b0, ex->b1, n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
-        m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, ex->err);
+        m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, vmax, seg_cols(m),
+        ex->err);
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
@@ -637,18 +655,27 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     return SAQ_OK;
 }
 
+SegCols seg_cols(const saq_model *m) {
+    SegCols c{};
+    c.nk = (int32_t)m->kept.size();
+    for (int i = 0; i < 64; ++i) c.end[i] = 0x7fffffff;
+    for (int i = 0; i < c.nk && i < 64; ++i) c.end[i] = m->kept[(size_t)i].off + m->kept[(size_t)i].len;
+    return c;
+}
+
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, float *O,
                              int64_t ldo, int layout, float *norms2, int64_t norms_stride,
-                             cudaStream_t s) {
+                             float *vmax, cudaStream_t s) {
     if (n <= 0) return SAQ_OK;
     if (((uintptr_t)X & 15u) != 0) return set_error(SAQ_ERR_INVALID, "X not 16-byte aligned");
+    if (m->kept.size() > 64) return set_error(SAQ_ERR_UNSUPPORTED, "more than 64 kept segments");
     switch (m->tc.precision) {
         case SAQ_PREC_FP32:
-            return launch_mode<kSplit>(m, X, n, O, ldo, layout, norms2, norms_stride, s);
+            return launch_mode<kSplit>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, s);
         case SAQ_PREC_BF16:
-            return launch_mode<kBF16>(m, X, n, O, ldo, layout, norms2, norms_stride, s);
+            return launch_mode<kBF16>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, s);
         case SAQ_PREC_FP8:
-            return launch_mode<kFP8>(m, X, n, O, ldo, layout, norms2, norms_stride, s);
+            return launch_mode<kFP8>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, s);
     }
     return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
 }

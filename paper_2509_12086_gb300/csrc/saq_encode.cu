@@ -35,28 +35,60 @@ bool use_tc(const saq_model *m) {
 
 }  // namespace
 
+namespace {
+// Scratch of an encode of up to `rows` rows: interleaved projected rows (FP32),
+// their codes during adjustment (bytes), and v_max per row and kept segment.
+struct ScratchParts {
+    float *Oi;
+    uint8_t *cs;
+    float *vmax;
+    size_t vmax_bytes;
+};
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+ScratchParts scratch_parts(const saq_model *m, void *scratch, int64_t rows) {
+    const size_t r32 = (size_t)((rows + 31) / 32 * 32);
+    const size_t elems = r32 * (size_t)std::max(1, m->dk);
+    uint8_t *b = static_cast<uint8_t *>(scratch);
+    ScratchParts p;
+    p.Oi = reinterpret_cast<float *>(b);
+    p.cs = b + align256(elems * sizeof(float));
+    p.vmax = reinterpret_cast<float *>(p.cs + align256(elems));
+    p.vmax_bytes = r32 * std::max<size_t>(1, m->kept.size()) * sizeof(float);
+    return p;
+}
+}  // namespace
+
 size_t encode_scratch_bytes(const saq_model *m, int64_t rows) {
-    const size_t elems = (size_t)((rows + 31) / 32 * 32) * (size_t)std::max(1, m->dk);
-    return ((elems * sizeof(float) + 255) & ~(size_t)255) + ((elems + 255) & ~(size_t)255);
+    const size_t r32 = (size_t)((rows + 31) / 32 * 32);
+    const size_t elems = r32 * (size_t)std::max(1, m->dk);
+    return align256(elems * sizeof(float)) + align256(elems) +
+           align256(r32 * std::max<size_t>(1, m->kept.size()) * sizeof(float));
 }
 
-// Projection of rows [0, n) into O and |x - c|^2 into norms (stride).
+// Projection of rows [0, n) into O and |x - c|^2 into norms (stride); with
+// the interleaved layout and vmax != NULL also v_max per row and segment.
 saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                        int layout, float *norms, int64_t nstride, cudaStream_t s) {
-    if (use_tc(m)) return launch_project_tc(m, X, n, O, ldo, layout, norms, nstride, s);
+                        int layout, float *norms, int64_t nstride, float *vmax, cudaStream_t s) {
+    if (use_tc(m)) {
+        if (vmax && layout == kInterleaved)
+            SAQ_CUDA_CHECK(cudaMemsetAsync(vmax, 0, sizeof(float) * (size_t)((n + 31) / 32 * 32) *
+                                                       m->kept.size(), s));
+        return launch_project_tc(m, X, n, O, ldo, layout, norms, nstride, vmax, s);
+    }
     saq_status st = launch_project_simt(m, X, n, O, ldo, layout, s);
     if (st != SAQ_OK) return st;
-    return launch_rownorm2(m, X, n, norms, nstride, s);
+    st = launch_rownorm2(m, X, n, norms, nstride, s);
+    if (st != SAQ_OK) return st;
+    if (vmax && layout == kInterleaved) st = launch_seg_vmax(m, O, n, vmax, s);
+    return st;
 }
 
-// Quantize rows [0, n) whose interleaved projection sits at the start of
+// Quantize rows [0, n) whose interleaved projection (and v_max) sit in
 // `scratch` (sized by encode_scratch_bytes for rows_cap rows).
 saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, int64_t n,
                          uint8_t *codes, float *factors, cudaStream_t s) {
-    const size_t elems = (size_t)((rows_cap + 31) / 32 * 32) * (size_t)std::max(1, m->dk);
-    float *Oi = static_cast<float *>(scratch);
-    uint8_t *cs = static_cast<uint8_t *>(scratch) + ((elems * sizeof(float) + 255) & ~(size_t)255);
-    return launch_caq1(m, Oi, n, cs, codes, factors, s);
+    const ScratchParts p = scratch_parts(m, scratch, rows_cap);
+    return launch_caq1(m, p.Oi, n, p.cs, p.vmax, codes, factors, s);
 }
 
 // The whole encode of rows [0, n) on stream s with a scratch for `rows` rows.
@@ -64,8 +96,9 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
                        float *factors, void *scratch, int64_t rows, cudaStream_t s) {
     for (int64_t r0 = 0; r0 < n; r0 += rows) {
         const int64_t nr = std::min(rows, n - r0);
-        saq_status st = project_rows(m, X + r0 * m->d, nr, static_cast<float *>(scratch), m->dk,
-                                     kInterleaved, factors + r0 * m->nf, m->nf, s);
+        const ScratchParts p = scratch_parts(m, scratch, rows);
+        saq_status st = project_rows(m, X + r0 * m->d, nr, p.Oi, m->dk, kInterleaved,
+                                     factors + r0 * m->nf, m->nf, p.vmax, s);
         if (st != SAQ_OK) return st;
         st = quantize_rows(m, scratch, rows, nr, codes + r0 * (int64_t)m->code_bytes,
                            factors + r0 * m->nf, s);
@@ -101,8 +134,9 @@ saq_status encode_rows_overlapped(saq_model *m, const float *X, int64_t n, uint8
         void *scr = b ? scratch1 : scratch0;
         const int64_t nr = std::min(rows, n - r0);
         if (i >= 2) SAQ_CUDA_CHECK(cudaStreamWaitEvent(ps, m->ev_caq[b], 0));
-        st = project_rows(m, X + r0 * m->d, nr, static_cast<float *>(scr), m->dk, kInterleaved,
-                          factors + r0 * m->nf, m->nf, ps);
+        const ScratchParts p = scratch_parts(m, scr, rows);
+        st = project_rows(m, X + r0 * m->d, nr, p.Oi, m->dk, kInterleaved,
+                          factors + r0 * m->nf, m->nf, p.vmax, ps);
         if (st != SAQ_OK) break;
         SAQ_CUDA_CHECK(cudaEventRecord(m->ev_proj[b], ps));
         SAQ_CUDA_CHECK(cudaStreamWaitEvent(qs, m->ev_proj[b], 0));
@@ -168,7 +202,7 @@ saq_status saq_project(const saq_model *m, const float *X_dev, int64_t n, float 
         return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
     saq_status st = check_device(m);
     if (st != SAQ_OK) return st;
-    return project_rows(m, X_dev, n, O_dev, m->dk, kRowMajor, norms2_dev, 1,
+    return project_rows(m, X_dev, n, O_dev, m->dk, kRowMajor, norms2_dev, 1, nullptr,
                         (cudaStream_t)stream);
 }
 
@@ -185,7 +219,7 @@ saq_status saq_project_ex(const saq_model *m, const float *X_dev, int64_t n, flo
         return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
     saq_status st = check_device(m);
     if (st != SAQ_OK) return st;
-    return project_rows(m, X_dev, n, O_dev, m->dk, kInterleaved, norms2_dev, 1,
+    return project_rows(m, X_dev, n, O_dev, m->dk, kInterleaved, norms2_dev, 1, nullptr,
                         (cudaStream_t)stream);
 }
 
@@ -207,12 +241,13 @@ saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
     cudaStream_t s = (cudaStream_t)stream;
     st = launch_copy_strided(norms2_dev, 1, factors_dev, m->nf, n, s);
     if (st != SAQ_OK || m->dk == 0) return st;
-    uint8_t *cs = nullptr;
-    const size_t cb = (size_t)((n + 31) / 32 * 32) * (size_t)m->dk;
-    if (cudaMallocAsync((void **)&cs, cb, s) != cudaSuccess)
+    void *scratch = nullptr;
+    if (cudaMallocAsync(&scratch, encode_scratch_bytes(m, n), s) != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed");
-    st = launch_caq1(m, O_dev, n, cs, codes_dev, factors_dev, s);
-    cudaFreeAsync(cs, s);
+    const ScratchParts p = scratch_parts(m, scratch, n);
+    st = launch_seg_vmax(m, O_dev, n, p.vmax, s);
+    if (st == SAQ_OK) st = launch_caq1(m, O_dev, n, p.cs, p.vmax, codes_dev, factors_dev, s);
+    cudaFreeAsync(scratch, s);
     return st;
 }
 
@@ -236,7 +271,9 @@ saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
     cudaError_t e = cudaMallocAsync(&scratch, encode_scratch_bytes(m, n), s);
     if (e != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
-    st = launch_interleave(O_dev, m->dk, n, m->dk, static_cast<float *>(scratch), s);
+    const ScratchParts p = scratch_parts(m, scratch, n);
+    st = launch_interleave(O_dev, m->dk, n, m->dk, p.Oi, s);
+    if (st == SAQ_OK) st = launch_seg_vmax(m, p.Oi, n, p.vmax, s);
     if (st == SAQ_OK) st = quantize_rows(m, scratch, n, n, codes_dev, factors_dev, s);
     cudaFreeAsync(scratch, s);
     return st;

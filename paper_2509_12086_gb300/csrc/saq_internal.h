@@ -51,6 +51,13 @@ struct TcOperands {
     void *extra = nullptr;    // tensor maps, padded mean, error word (k_tc.cu)
 };
 
+// Column ends of the kept segments in the projected (kept) space, for the
+// per-(row, segment) v_max of the projection epilogue.
+struct SegCols {
+    int32_t end[64];
+    int32_t nk;
+};
+
 }  // namespace saq
 
 struct saq_model {
@@ -101,10 +108,14 @@ enum { kRowMajor = 0, kInterleaved = 1 };
 // O[i, :] = W (x_i - c) for rows [0, n): FP32 SIMT GEMM, exact FP32 products.
 saq_status launch_project_simt(const saq_model *m, const float *X, int64_t n,
                                float *O, int64_t ldo, int layout, cudaStream_t s);
-// Tensor-core projection (tcgen05 + TMA); precision from m->tc.
+// Tensor-core projection (tcgen05 + TMA); precision from m->tc.  With the
+// interleaved layout and vmax != NULL it also writes, per row and kept
+// segment, max |o| into vmax (interleaved like O: [(row/32) * nk + s] * 32 +
+// row % 32; the caller zeroes it first).
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n,
                              float *O, int64_t ldo, int layout, float *norms2,
-                             int64_t norms_stride, cudaStream_t s);
+                             int64_t norms_stride, float *vmax, cudaStream_t s);
+SegCols seg_cols(const saq_model *m);
 bool tc_supported(const saq_model *m);
 void tc_release(saq_model *m);
 // Reads and clears the device error word of the tensor-core projection
@@ -119,16 +130,20 @@ saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
 // Quantize + adjust + pack every kept segment for rows [0, n) of interleaved
 // projected rows Oi, with a byte scratch cs of the same layout (k_caq1.cu).
 saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
-                       uint8_t *codes, float *factors, cudaStream_t s);
+                       const float *vmax, uint8_t *codes, float *factors, cudaStream_t s);
+// vmax of every (row, kept segment) from interleaved rows Oi (k_caq1.cu).
+saq_status launch_seg_vmax(const saq_model *m, const float *Oi, int64_t n, float *vmax,
+                           cudaStream_t s);
 // Row-major O -> interleaved Oi.
 saq_status launch_interleave(const float *O, int64_t ldo, int64_t n, int dk, float *Oi,
                              cudaStream_t s);
 // Scratch of an encode of up to `rows` rows: the interleaved projected rows
 // (FP32) followed by the byte code scratch (saq_encode.cu).
 size_t encode_scratch_bytes(const saq_model *m, int64_t rows);
-// Projection of rows [0, n) (saq_encode.cu).
+// Projection of rows [0, n) (saq_encode.cu); vmax as for launch_project_tc
+// (may be NULL).
 saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                        int layout, float *norms, int64_t nstride, cudaStream_t s);
+                        int layout, float *norms, int64_t nstride, float *vmax, cudaStream_t s);
 // Quantization of rows [0, n) from interleaved projected rows in `scratch`.
 saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, int64_t n,
                          uint8_t *codes, float *factors, cudaStream_t s);

@@ -53,16 +53,20 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
     d = 960
     model = P.saq_fit(synth.power_law(5000, d, 0.8, device="cuda"), avg_bits=4.0)
     assert model.d_kept == 960
-    # 32 MiB holds 5 bytes per row and kept dimension, rows in groups of 32:
-    # 218 groups = 6,976 rows fit at d_kept = 960, one more row does not
-    X = synth.power_law(6977, d, 0.8, seed=303, device="cuda")
-    codes, factors = model.alloc_outputs(6977)
+    nseg = sum(1 for _, _, b in model.plan if b > 0)
+    # 32 MiB holds 5 bytes per row and kept dimension plus 4 per row and kept
+    # segment, rows in groups of 32
+    per_row = 5 * model.d_kept + 4 * nseg
+    most = (32 << 20) // (per_row * 32) * 32
+    X = synth.power_law(most + 1, d, 0.8, seed=303, device="cuda")
+    codes, factors = model.alloc_outputs(most + 1)
     rc = _call_noalloc(model, X, codes, factors)
     assert rc == 1
     msg = P.load().saq_last_error()
-    assert b"exceeds the no-allocation scratch" in msg and b"at most 6976 rows" in msg
-    rc = _call_noalloc(model, X[:6976], codes[:6976], factors[:6976])
+    assert b"exceeds the no-allocation scratch" in msg
+    assert ("at most %d rows" % most).encode() in msg
+    rc = _call_noalloc(model, X[:most], codes[:most], factors[:most])
     assert rc == 0, P.load().saq_last_error()
-    ref_codes, ref_factors = model.encode(X[:6976].contiguous())
+    ref_codes, ref_factors = model.encode(X[:most].contiguous())
     torch.cuda.synchronize()
-    assert torch.equal(codes[:6976, :model.code_bytes], ref_codes)
+    assert torch.equal(codes[:most, :model.code_bytes], ref_codes)
