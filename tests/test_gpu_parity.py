@@ -42,7 +42,8 @@ def check_codes(mo, eo, codes_gpu, factors_gpu, agree_min=CODE_AGREE, margin=MAR
     `margin` (a near-tie that FP32 may resolve the other way); past such a
     decision both trajectories are correct CAQ results, so there the GPU
     result is checked for validity instead: its cosine is at least the
-    initial code's and within 1e-3 of the oracle's.  The per-vector error
+    initial code's (to the 1e-5 of the FP32 factor) and within 1e-3 of the
+    oracle's.  The per-vector error
     bar applies to every vector without an excused mismatch."""
     codes = O.unpack(codes_gpu, mo)
     # padding bits of the packed planes are zero: pack(unpack(x)) == x
@@ -65,7 +66,8 @@ def check_codes(mo, eo, codes_gpu, factors_gpu, agree_min=CODE_AGREE, margin=MAR
     cg, co = f[:, 2::2], ref[:, 2::2]
     assert np.all((np.abs(cg - co) <= 1e-5) | mism), "cos factor off where codes agree"
     if mism.any():
-        assert np.all(cg[mism] >= eo.init_cos[mism] - 1e-6)
+        # the FP32 cosine factor carries ~1e-6 rounding per 1000 coordinates
+        assert np.all(cg[mism] >= eo.init_cos[mism] - 1e-5)
         assert np.all(np.abs(cg[mism] - co[mism]) <= 1e-3)
     clean = ~mism.any(axis=1)
     eg, eo_ = O.quant_error(f, mo), O.quant_error(ref, mo)
