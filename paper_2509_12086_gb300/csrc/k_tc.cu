@@ -18,8 +18,14 @@
 // three or more stages fit in shared memory.
 // Precision modes:
 //   kSplit  FP32: A = a_hi + a_lo and B = b_hi + b_lo as FP16 pairs (scaled by
-//           powers of two), D = a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32
-//           accumulation (error of the order of FP32 rounding);
+//           powers of two), D = a_hi b_hi + (a_hi b_lo + a_lo b_hi) with FP32
+//           accumulation.  The tensor core's accumulation is not rounded to
+//           nearest: each MMA shrinks the accumulator by a fraction of an
+//           FP32 ulp, which over K = 3072 in one accumulator (576 MMAs) came
+//           to a 1e-5 loss of |o|.  The two correction products therefore go
+//           to a second accumulator (TMEM columns 256..511, 2^-11 of the
+//           main term, so its own loss does not count), the main one takes
+//           a third of the MMAs, and the epilogue adds the two in FP32;
 //   kBF16   one BF16 product;
 //   kFP8    one E4M3 product (kind::f8f6f4), per-segment scales on W.
 // All waits are bounded (about 2 s); a timed-out wait raises an error flag,
@@ -46,7 +52,7 @@ enum Mode { kSplit = 0, kBF16 = 1, kFP8 = 2 };
 
 constexpr int kBM = 128;            // rows per tile (UMMA M)
 constexpr int kNPMax = 256;         // output columns per tile at most (UMMA N)
-constexpr int kTmemCols = 256;
+constexpr int kAcc2 = 256;          // TMEM column of the split mode's correction accumulator
 constexpr int kConvWarps = 8;
 constexpr int kThreads = 64 + 32 * kConvWarps;
 constexpr uint32_t kXBox = 16384;   // 128 rows x 128 bytes of staged FP32
@@ -55,13 +61,13 @@ constexpr uint32_t kBTile = 16384;  // 256 rows x 64 bytes
 
 template <int MODE> struct Cfg;
 template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage
-    static constexpr int BK = 32, STAGES = 3, NA = 2, XBOX = 1;
+    static constexpr int BK = 32, STAGES = 3, NA = 2, XBOX = 1, TMEM = 512;
 };
 template <> struct Cfg<kBF16> {
-    static constexpr int BK = 32, STAGES = 4, NA = 1, XBOX = 1;
+    static constexpr int BK = 32, STAGES = 4, NA = 1, XBOX = 1, TMEM = 256;
 };
 template <> struct Cfg<kFP8> {  // 64 E4M3 per row per stage
-    static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2;
+    static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2, TMEM = 256;
 };
 
 template <int MODE> constexpr uint32_t stage_bytes() {
@@ -71,6 +77,11 @@ template <int MODE> constexpr uint32_t a_offset() { return (uint32_t)Cfg<MODE>::
 template <int MODE> constexpr uint32_t b_offset() {
     return a_offset<MODE>() + (uint32_t)Cfg<MODE>::NA * kATile;
 }
+// A CTA that allocates all 512 TMEM columns must be alone on its SM (an
+// allocation beyond the free columns waits for a co-resident CTA to free
+// its own): its stages alone take more than half of the 228 KB of an SM.
+static_assert(Cfg<kSplit>::STAGES * stage_bytes<kSplit>() > 228u * 1024u / 2u,
+              "two split-mode CTAs per SM would share 512 TMEM columns");
 // dynamic shared memory: stages, barriers and the row-norm halves, -c*s
 template <int MODE> uint32_t smem_bytes(int dpad) {
     return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + 640 + 4u * (uint32_t)dpad;
@@ -252,7 +263,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(C::TMEM)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -308,8 +319,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
                     const uint64_t off = (uint64_t)(kk * 2);
                     umma<MODE>(tmem, a0 + off, b0 + off, idesc, (kb | kk) != 0);
                     if (C::NA == 2) {
-                        umma<MODE>(tmem, a0 + off, b1 + off, idesc, 1u);
-                        umma<MODE>(tmem, a1 + off, b0 + off, idesc, 1u);
+                        umma<MODE>(tmem + kAcc2, a0 + off, b1 + off, idesc, (kb | kk) != 0);
+                        umma<MODE>(tmem + kAcc2, a1 + off, b0 + off, idesc, 1u);
                     }
                 }
                 umma_commit(&empty[s]);
@@ -427,6 +438,12 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
             for (int c = cbeg & ~15; c < cend; c += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                if (C::NA == 2) {
+                    float v2[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcc2 + c), v2);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += v2[i];
+                }
                 if (!row_ok) continue;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -462,7 +479,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
         __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
+                     "r"(C::TMEM)
                      : "memory");
     }
 }
