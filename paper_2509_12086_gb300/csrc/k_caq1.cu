@@ -6,21 +6,23 @@
 // over the coordinates of the segment: step j loads coordinate j of all 32
 // vectors (one coalesced 128-byte line of the projected rows, stored
 // interleaved by groups of 32 rows: O_i[(g * d_kept + col) * 32 + lane]) and
-// their current codes (a byte scratch with the same layout), tests +Delta then
-// -Delta for each lane against that lane's own state, and applies the lane's
-// move.  Each lane therefore executes the paper's sequential scan exactly, and
-// an accepted move costs a predicated update instead of a serialising pass.
+// their current codes (a byte scratch with the same layout), decides the
+// lane's move against that lane's own state and applies it.  Each lane
+// therefore executes the paper's sequential scan exactly, and an accepted
+// move costs a predicated update instead of a serialising pass.
 //
-// Decision in closed form (as in k_caq.cu): with I = <u, o> > 0,
-// S = |u|^2, u = 2c - (2^B - 1), moving u_i by 2s raises I/sqrt(S) iff
-//     s*o_i*alpha + o_i^2*beta > s*u_i + 1,   alpha = S/I, beta = S/I^2.
-// At most one of the two moves can raise the cosine (the superlevel set of the
-// cosine is a convex cone), and the paper's -Delta trial after an accepted
-// +Delta returns to the old point and is rejected.  A lane whose round made no
-// move stops (its state no longer changes).  v_max comes from the projection
-// (or a separate pass), so the rows are streamed once for the initial codes
-// and once per round; S is tracked exactly as an integer, I in FP32, and the
-// bit-planes are packed from the codes alone.
+// Decision in closed form, without a division: with I = <u, o> > 0,
+// S = |u|^2 and u = 2c - (2^B - 1), moving u_i by 2s (s = +-1) raises
+// I^2 / S iff (I + 2 s o_i)^2 S > I^2 (S + 4 s u_i + 4), i.e. iff
+//     s T I + o_i^2 S > I^2,   T = o_i S - u_i I.
+// Only s = sign(T) can pass (the other side is smaller by 2|T|I), which is
+// the convex-cone fact that at most one of +-Delta raises the cosine; the
+// paper's -Delta trial after an accepted +Delta returns to the old point and
+// is rejected.  A lane whose round made no move stops (its state no longer
+// changes).  v_max comes from the projection (or a separate pass).  Every
+// pass over the coordinates keeps kU loads in flight.  I and S are tracked in
+// FP32 for the decisions; S is recounted exactly from the final codes while
+// they are packed into bit-planes.
 #include <algorithm>
 
 #include "saq_internal.h"
@@ -29,7 +31,7 @@ namespace saq {
 
 namespace {
 
-constexpr int kU = 8;  // prefetch depth of the adjustment loop
+constexpr int kU = 8;  // loads in flight per lane in every pass
 constexpr int kMaxSeg = 64;
 
 struct Seg {
@@ -42,27 +44,42 @@ struct SegTable {
 };
 
 // Bit-planes of one lane's segment from its codes (most significant first,
-// 64-bit words).
+// 64-bit words); returns |u|^2 of the codes, exactly.
 template <int B>
-__device__ __forceinline__ void pack_segment(const uint8_t *cp, int len, bool valid,
-                                             uint64_t *cout, int words) {
+__device__ __forceinline__ int pack_segment(const uint8_t *cp, int len, bool valid,
+                                            uint64_t *cout, int words) {
+    constexpr int cmax = (1 << B) - 1;
     uint64_t w[B];
 #pragma unroll
     for (int p = 0; p < B; ++p) w[p] = 0ull;
-    for (int j = 0; j < len; ++j) {
-        const int c = cp[(int64_t)j << 5];
-        const int bp = j & 63;
+    int S = 0;
+    for (int j0 = 0; j0 < len; j0 += kU) {
+        int c[kU];
 #pragma unroll
-        for (int p = 0; p < B; ++p) w[p] |= (uint64_t)((c >> (B - 1 - p)) & 1) << bp;
-        if (bp == 63 || j == len - 1) {
+        for (int k = 0; k < kU; ++k) c[k] = j0 + k < len ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
+        // plane p of the kU codes as the bits of one byte (past the end: 0)
+#pragma unroll
+        for (int p = 0; p < B; ++p) {
+            uint32_t b = 0;
+#pragma unroll
+            for (int k = 0; k < kU; ++k) b |= (uint32_t)((c[k] >> (B - 1 - p)) & 1) << k;
+            w[p] |= (uint64_t)b << (j0 & 63);
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int u = 2 * c[k] - cmax;
+            S += j0 + k < len ? u * u : 0;
+        }
+        if (((j0 + kU) & 63) == 0 || j0 + kU >= len) {
             if (valid) {
 #pragma unroll
-                for (int p = 0; p < B; ++p) cout[p * words + (j >> 6)] = w[p];
+                for (int p = 0; p < B; ++p) cout[p * words + (j0 >> 6)] = w[p];
             }
 #pragma unroll
             for (int p = 0; p < B; ++p) w[p] = 0ull;
         }
     }
+    return S;
 }
 
 // One warp per (kept segment, group of 32 rows); all kept segments of a
@@ -94,22 +111,27 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
     const float inv_delta = live ? (float)(1 << (B - 1)) / vmax : 0.f;
     float I = 0.f, n2 = 0.f;
     int Si = 0;
-    for (int j = 0; j < len; ++j) {
-        const float x = valid ? __ldg(op + ((int64_t)j << 5)) : 0.f;
-        int c = 0;
-        if (live) {
-            c = (int)floorf((x + vmax) * inv_delta);
-            c = c < 0 ? 0 : (c > cmax ? cmax : c);
+    for (int j0 = 0; j0 < len; j0 += kU) {
+        float x[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            x[k] = valid && j0 + k < len ? __ldg(op + ((int64_t)(j0 + k) << 5)) : 0.f;
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            if (j0 + k >= len) break;
+            int c = 0;
+            if (live) {
+                c = (int)floorf((x[k] + vmax) * inv_delta);
+                c = c < 0 ? 0 : (c > cmax ? cmax : c);
+            }
+            cp[(int64_t)(j0 + k) << 5] = (uint8_t)c;
+            const int u = 2 * c - cmax;
+            I = fmaf((float)u, x[k], I);
+            n2 = fmaf(x[k], x[k], n2);
+            Si += u * u;
         }
-        cp[(int64_t)j << 5] = (uint8_t)c;
-        const int u = 2 * c - cmax;
-        I = fmaf((float)u, x, I);
-        n2 = fmaf(x, x, n2);
-        Si += u * u;
     }
-    float Sf = (float)Si;
-    float rI = live ? __fdividef(1.f, I) : 0.f;
-    float alpha = Sf * rI, beta = alpha * rI;
+    float S = (float)Si, I2 = I * I;
     bool active = live;
     for (int r = 0; r < rounds; ++r) {
         if (!__any_sync(0xffffffffu, active)) break;
@@ -138,20 +160,17 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
                 const float x = xb[k];
                 const int c = cb[k];
                 const float u = (float)(2 * c - cmax);
-                const float t = x * x * beta;
-                const bool in = active && (j0 + k < len);
-                const bool ap = in && (c < cmax) && (fmaf(x, alpha, t) > u + 1.f);
-                const bool am = in && !ap && (c > 0) && (fmaf(-x, alpha, t) > 1.f - u);
-                if (ap || am) {
-                    const float sg = ap ? 1.f : -1.f;
-                    I = fmaf(2.f * sg, x, I);
-                    Sf += fmaf(4.f * sg, u, 4.f);
-                    const int ui = 2 * c - cmax;  // |u|^2 changes by 4su + 4, exactly
-                    Si += ap ? 4 * ui + 4 : 4 - 4 * ui;
-                    rI = __fdividef(1.f, I);
-                    alpha = Sf * rI;
-                    beta = alpha * rI;
-                    cp[(int64_t)(j0 + k) << 5] = (uint8_t)(ap ? c + 1 : c - 1);
+                const float xS = x * S;
+                const float T = fmaf(-u, I, xS);
+                const bool up = T > 0.f;
+                const bool ok = active && (j0 + k < len) && (up ? c < cmax : c > 0) &&
+                                fmaf(fabsf(T), I, x * xS) > I2;
+                if (ok) {
+                    const float s2 = up ? 2.f : -2.f;
+                    I = fmaf(s2, x, I);
+                    S = fmaf(2.f * s2, u, S + 4.f);
+                    I2 = I * I;
+                    cp[(int64_t)(j0 + k) << 5] = (uint8_t)(up ? c + 1 : c - 1);
                     moved = true;
                 }
             }
@@ -167,14 +186,14 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
     // bit-planes from the codes (most significant first, 64-bit words)
     uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
     switch (B) {  // uniform per warp
-        case 1: pack_segment<1>(cp, len, valid, cout, words); break;
-        case 2: pack_segment<2>(cp, len, valid, cout, words); break;
-        case 3: pack_segment<3>(cp, len, valid, cout, words); break;
-        case 4: pack_segment<4>(cp, len, valid, cout, words); break;
-        case 5: pack_segment<5>(cp, len, valid, cout, words); break;
-        case 6: pack_segment<6>(cp, len, valid, cout, words); break;
-        case 7: pack_segment<7>(cp, len, valid, cout, words); break;
-        default: pack_segment<8>(cp, len, valid, cout, words); break;
+        case 1: Si = pack_segment<1>(cp, len, valid, cout, words); break;
+        case 2: Si = pack_segment<2>(cp, len, valid, cout, words); break;
+        case 3: Si = pack_segment<3>(cp, len, valid, cout, words); break;
+        case 4: Si = pack_segment<4>(cp, len, valid, cout, words); break;
+        case 5: Si = pack_segment<5>(cp, len, valid, cout, words); break;
+        case 6: Si = pack_segment<6>(cp, len, valid, cout, words); break;
+        case 7: Si = pack_segment<7>(cp, len, valid, cout, words); break;
+        default: Si = pack_segment<8>(cp, len, valid, cout, words); break;
     }
     if (valid) {
         float *fo = factors + v * nf;
