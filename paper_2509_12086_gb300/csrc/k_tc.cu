@@ -4,7 +4,12 @@
 // One CTA computes a 128-row x NP-column tile of O (NP <= 256, a multiple of
 // 16 chosen per model so that the column passes are balanced) over K = d:
 //   warp 0      TMA producer: the FP32 X tile (128 rows x 32 values per box,
-//               128-byte swizzle, staged) and the W operand tile(s);
+//               128-byte swizzle, staged) and the W operand tile(s).  W is a
+//               model constant, stored in global memory already cut into
+//               the (pass, K block) tiles of the shared-memory layout the
+//               MMA reads (NP rows of 64 bytes, 64-byte swizzle), so each
+//               operand tile is one contiguous bulk copy instead of NP
+//               64-byte rows of a tensor copy;
 //   warp 1      TMEM owner and MMA issuer (one elected lane): tcgen05.mma,
 //               accumulator 128 lanes x NP FP32 columns in TMEM;
 //   warps 2-9   converters, then epilogue.  Two threads per tile row (one per
@@ -52,6 +57,7 @@ enum Mode { kSplit = 0, kBF16 = 1, kFP8 = 2 };
 
 constexpr int kBM = 128;            // rows per tile (UMMA M)
 constexpr int kNPMax = 256;         // output columns per tile at most (UMMA N)
+constexpr int kPrefetch = 8;        // X boxes are prefetched into L2 this many K blocks ahead
 constexpr int kAcc2 = 256;          // TMEM column of the split mode's correction accumulator
 constexpr int kConvWarps = 8;
 constexpr int kThreads = 64 + 32 * kConvWarps;
@@ -144,6 +150,22 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+// pull a box of the tensor into L2 ahead of its load (no shared memory)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     (uint64_t)map),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+// contiguous global -> shared copy (16-byte aligned, a multiple of 16 bytes)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -204,6 +226,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// both accumulators of the split mode, one wait (one asm statement, so no
+// register is read before the loads have landed)
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&v)[16],
+                                            float (&w)[16]) {
+    uint32_t r[16], q[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+        "%28,%29,%30,%31}, [%33];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]),
+          "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]),
+          "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = __uint_as_float(r[i]);
+        w[i] = __uint_as_float(q[i]);
+    }
+}
 __device__ __forceinline__ void named_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -224,8 +270,8 @@ __device__ __forceinline__ uint32_t swz64(int r, int c) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmb0,
-          const __grid_constant__ CUtensorMap tmb1, int64_t n, int dk, int npass, int np, int nkb,
+k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ wt0,
+          const uint8_t *__restrict__ wt1, int64_t n, int dk, int npass, int np, int nkb,
           const float *__restrict__ mcs_g, float x_scale, const float *__restrict__ col_scale,
           float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms,
           int64_t nstride, float *__restrict__ vmax, const SegCols segc,
@@ -275,8 +321,12 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
     if (warp == 0) {
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmx) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmb0) : "memory");
             const uint32_t tx = (uint32_t)C::XBOX * kXBox + (uint32_t)C::NA * (uint32_t)np * 64u;
+            // X boxes kPrefetch K blocks ahead are pulled into L2, so that the
+            // stage loads wait on L2 rather than on HBM
+            for (int kb = C::STAGES; kb < kPrefetch && kb < nkb; ++kb)
+#pragma unroll
+                for (int b = 0; b < C::XBOX; ++b) tma_prefetch_2d(&tmx, kb * C::BK + b * 32, (int)row0);
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % C::STAGES;
@@ -288,8 +338,13 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
                 for (int b = 0; b < C::XBOX; ++b)
                     tma_load_2d(st + b * kXBox, &tmx, kb * C::BK + b * 32, (int)row0, &full[s]);
                 uint8_t *bs = st + b_offset<MODE>();
-                tma_load_2d(bs, &tmb0, kb * C::BK, col0, &full[s]);
-                if (C::NA == 2) tma_load_2d(bs + kBTile, &tmb1, kb * C::BK, col0, &full[s]);
+                const int64_t wo = ((int64_t)pass * nkb + kb) * np * 64;
+                bulk_load(bs, wt0 + wo, (uint32_t)np * 64u, &full[s]);
+                if (C::NA == 2) bulk_load(bs + kBTile, wt1 + wo, (uint32_t)np * 64u, &full[s]);
+                if (kb + kPrefetch < nkb)
+#pragma unroll
+                    for (int b = 0; b < C::XBOX; ++b)
+                        tma_prefetch_2d(&tmx, (kb + kPrefetch) * C::BK + b * 32, (int)row0);
                 issued = kb + 1;
             }
             // drain: the last loads of each stage must land before the CTA exits
@@ -426,40 +481,70 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUten
             float *orow = O + (row0 + r) * ldo;
             // interleaved: column `col` of row R at ((R / 32) * dk + col) * 32 + R % 32
             float *ogrp = O + (((row0 + r) >> 5) * (int64_t)dk << 5) + lane;
-            const int half = np >> 1;  // a multiple of 8
-            const int cbeg = h * half, cend = cbeg + half;
             // running max |o| of the current kept segment (interleaved layout only)
             const bool want_vmax = il && vmax != nullptr;
             float *vgrp = want_vmax ? vmax + (((row0 + r) >> 5) * (int64_t)segc.nk << 5) + lane
                                     : nullptr;
+            const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
             int si = 0;
             float mx = 0.f;
+            // 16-column chunks, alternating between the two threads of a row
 #pragma unroll 1
-            for (int c = cbeg & ~15; c < cend; c += 16) {
+            for (int ch = h; ch < (np >> 4); ch += 2) {
+                const int c = ch << 4;
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
                 if (C::NA == 2) {
                     float v2[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcc2 + c), v2);
+                    tmem_ld16x2(tq + (uint32_t)c, tq + (uint32_t)(kAcc2 + c), v, v2);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += v2[i];
+                } else {
+                    tmem_ld16(tq + (uint32_t)c, v);
                 }
-                if (!row_ok) continue;
+                const int cb = col0 + c;  // first output column of the chunk
+                if (!row_ok || cb >= dk) continue;
+                const int cn = min(16, dk - cb);
+                const float4 *sc4 = reinterpret_cast<const float4 *>(col_scale + cb);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int cc = c + i;
-                    const int col = col0 + cc;
-                    if (cc < cbeg || cc >= cend || col >= dk) continue;
-                    const float val = v[i] * col_scale[col];
-                    if (il) ogrp[(int64_t)col << 5] = val;
-                    else orow[col] = val;
-                    if (want_vmax) {
-                        while (col >= segc.end[si]) {
-                            if (mx > 0.f) atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
-                            mx = 0.f;
-                            ++si;
+                for (int i = 0; i < 4; ++i) {
+                    const float4 sc = __ldg(sc4 + i);
+                    v[4 * i] *= sc.x; v[4 * i + 1] *= sc.y; v[4 * i + 2] *= sc.z; v[4 * i + 3] *= sc.w;
+                }
+                if (cn == 16) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
+                        else orow[cb + i] = v[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (i >= cn) break;
+                        if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
+                        else orow[cb + i] = v[i];
+                    }
+                }
+                if (want_vmax) {
+                    while (cb >= segc.end[si]) {
+                        if (mx > 0.f) atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+                        mx = 0.f;
+                        ++si;
+                    }
+                    if (cb + cn <= segc.end[si]) {  // the chunk lies in one segment
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) mx = fmaxf(mx, i < cn ? fabsf(v[i]) : 0.f);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            if (i >= cn) break;
+                            while (cb + i >= segc.end[si]) {
+                                if (mx > 0.f)
+                                    atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+                                mx = 0.f;
+                                ++si;
+                            }
+                            mx = fmaxf(mx, fabsf(v[i]));
                         }
-                        mx = fmaxf(mx, fabsf(val));
                     }
                 }
             }
@@ -520,7 +605,6 @@ saq_status make_map(CUtensorMap *map, CUtensorMapDataType type, int elem, const 
 }
 
 struct TcExtra {
-    CUtensorMap b0, b1;
     float *mcs = nullptr;  // -c * x_scale, padded to the K blocks
     float x_scale = 1.f;
     int np = 0, npass = 0;
@@ -528,6 +612,29 @@ struct TcExtra {
 };
 
 double pow2_near(double x) { return ldexp(1.0, (int)lround(log2(x))); }
+
+// W operand (dkpad rows x dpad values, K-major) cut into the tiles the kernel
+// copies whole: tile (pass p, K block kb) holds rows p*np .. p*np + np - 1,
+// values kb*bk .. kb*bk + bk - 1, one 64-byte row each, with the 16-byte
+// chunks of row r permuted as the MMA's 64-byte swizzle expects
+// (chunk c at r * 64 + ((c ^ ((r >> 1) & 3)) * 16)).
+template <typename T>
+std::vector<T> tile_operand(const std::vector<T> &w, int dkpad, int dpad, int np, int bk) {
+    static_assert(sizeof(T) == 1 || sizeof(T) == 2, "operand element of 1 or 2 bytes");
+    constexpr int per_chunk = 16 / (int)sizeof(T);
+    const int npass = dkpad / np, nkb = dpad / bk;
+    std::vector<T> t(w.size());
+    for (int p = 0; p < npass; ++p)
+        for (int kb = 0; kb < nkb; ++kb)
+            for (int r = 0; r < np; ++r)
+                for (int c = 0; c < 4; ++c) {
+                    const size_t dst = (((size_t)p * nkb + kb) * np * 64 + (size_t)r * 64 +
+                                        (size_t)((c ^ ((r >> 1) & 3)) * 16)) / sizeof(T);
+                    const size_t src = ((size_t)p * np + r) * dpad + (size_t)kb * bk + (size_t)c * per_chunk;
+                    for (int e = 0; e < per_chunk; ++e) t[dst + e] = w[src + e];
+                }
+    return t;
+}
 
 template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, int64_t n,
                                            float *O, int64_t ldo, int layout, float *norms,
@@ -545,7 +652,8 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
     const int64_t blocks = tiles * ex->npass;
     if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
     k_proj_tc<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(
-        tmx, ex->b0, ex->b1, n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
+        tmx, (const uint8_t *)m->tc.w_hi,
+        (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi), n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
         m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, vmax, seg_cols(m),
         ex->err);
     note_launches();
@@ -609,6 +717,8 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
                 hi[(size_t)i * dpad + k] = h;
                 lo[(size_t)i * dpad + k] = __double2half(w - (double)__half2float(h));
             }
+        hi = tile_operand(hi, dkpad, dpad, np, BK);
+        lo = tile_operand(lo, dkpad, dpad, np, BK);
         SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_hi, hi.size() * 2));
         SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_lo, lo.size() * 2));
         SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice));
@@ -619,6 +729,7 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
         for (int i = 0; i < dk; ++i)
             for (int k = 0; k < d; ++k)
                 b[(size_t)i * dpad + k] = __float2bfloat16((float)m->W[(size_t)i * d + k]);
+        b = tile_operand(b, dkpad, dpad, np, BK);
         SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_hi, b.size() * 2));
         SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_hi, b.data(), b.size() * 2, cudaMemcpyHostToDevice));
         for (int i = 0; i < dk; ++i) cs[(size_t)i] = 1.f;
@@ -639,6 +750,7 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
                 cs[(size_t)i] = (float)(1.0 / (xs * sb));
             }
         }
+        b = tile_operand(b, dkpad, dpad, np, BK);
         SAQ_CUDA_CHECK(cudaMalloc(&m->tc.w_hi, b.size()));
         SAQ_CUDA_CHECK(cudaMemcpy(m->tc.w_hi, b.data(), b.size(), cudaMemcpyHostToDevice));
     } else {
@@ -655,20 +767,6 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     SAQ_CUDA_CHECK(cudaMemcpy(ex->mcs, mp.data(), sizeof(float) * mp.size(), cudaMemcpyHostToDevice));
     SAQ_CUDA_CHECK(cudaMalloc(&ex->err, sizeof(int)));
     SAQ_CUDA_CHECK(cudaMemset(ex->err, 0, sizeof(int)));
-    const bool f8 = precision == SAQ_PREC_FP8;
-    const CUtensorMapDataType t = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                                     : (precision == SAQ_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-    const int es = f8 ? 1 : 2;
-    saq_status st = make_map(&ex->b0, t, es, m->tc.w_hi, (uint64_t)dpad, (uint64_t)dkpad,
-                             (uint32_t)BK, (uint32_t)np, CU_TENSOR_MAP_SWIZZLE_64B);
-    if (st != SAQ_OK) return st;
-    ex->b1 = ex->b0;
-    if (m->tc.w_lo) {
-        st = make_map(&ex->b1, t, es, m->tc.w_lo, (uint64_t)dpad, (uint64_t)dkpad, (uint32_t)BK,
-                      (uint32_t)np, CU_TENSOR_MAP_SWIZZLE_64B);
-        if (st != SAQ_OK) return st;
-    }
     return SAQ_OK;
 }
 

@@ -43,8 +43,8 @@ struct KeptSeg {
 // Device operands of the tensor-core projection (built per precision).
 struct TcOperands {
     int precision = -1;
-    void *w_hi = nullptr;     // dk_pad x d_pad  (FP16 hi / BF16 / FP8)
-    void *w_lo = nullptr;     // dk_pad x d_pad  (FP16 lo) or nullptr
+    void *w_hi = nullptr;     // dk_pad x d_pad, cut into (pass, K block) tiles (FP16 hi / BF16 / FP8)
+    void *w_lo = nullptr;     // the same for the FP16 lo part, or nullptr
     float *col_scale = nullptr;  // per output column dequant scale (dk_pad)
     int dk_pad = 0;
     int d_pad = 0;
