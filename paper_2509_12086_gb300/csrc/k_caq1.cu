@@ -18,8 +18,8 @@
 // Only s = sign(T) can pass (the other side is smaller by 2|T|I), which is
 // the convex-cone fact that at most one of +-Delta raises the cosine; the
 // paper's -Delta trial after an accepted +Delta returns to the old point and
-// is rejected.  A lane whose round made no move stops (its state no longer
-// changes).  v_max comes from the projection (or a separate pass).  Every
+// is rejected.  The range check of c + s reads s*u < 2^B - 1.  A lane whose
+// round made no move stops (its state no longer changes).  v_max comes from the projection (or a separate pass).  Every
 // pass over the coordinates keeps kU loads in flight.  I and S are tracked in
 // FP32 for the decisions; S is recounted exactly from the final codes while
 // they are packed into bit-planes.
@@ -131,10 +131,32 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
             Si += u * u;
         }
     }
-    float S = (float)Si, I2 = I * I;
-    bool active = live;
+    // A lane that is done (no move in its last round, or nothing to adjust)
+    // keeps I2 = +inf, which no gain exceeds.
+    float S = (float)Si, I2 = live ? I * I : __int_as_float(0x7f800000);
+    const float cmaxf = (float)cmax;
+    // one coordinate of Algorithm 1 for this lane.  u = 2c - cmax as a float
+    // without a conversion: the bits 0x4B400000 + (2c - cmax) are the float
+    // 1.5 * 2^23 + (2c - cmax) exactly (unit spacing there).  s = sign(T)
+    // (+ for T = +0); s*u < cmax is the range check of c + s.
+    const int ubias = 0x4B400000 - cmax;
+    auto step = [&](float x, int c, int j, bool &moved) {
+        const float u = __int_as_float(ubias + 2 * c) - 12582912.f;
+        const float xS = x * S;
+        const float T = fmaf(-u, I, xS);
+        const uint32_t sgn = __float_as_uint(T) & 0x80000000u;
+        const float su = __uint_as_float(__float_as_uint(u) ^ sgn);
+        if (su < cmaxf && fmaf(fabsf(T), I, x * xS) > I2) {
+            I = fmaf(__uint_as_float(0x40000000u | sgn), x, I);
+            S = fmaf(4.f, su, S + 4.f);
+            I2 = I * I;
+            cp[(int64_t)j << 5] = (uint8_t)(sgn ? c - 1 : c + 1);
+            moved = true;
+        }
+    };
+    const int lenU = len & ~(kU - 1);  // coordinates in whole batches
     for (int r = 0; r < rounds; ++r) {
-        if (!__any_sync(0xffffffffu, active)) break;
+        if (!__any_sync(0xffffffffu, I2 != __int_as_float(0x7f800000))) break;
         bool moved = false;
         // software pipeline: coordinates j0 + U .. j0 + 2U - 1 are loaded before
         // j0 .. j0 + U - 1 are processed (a code is only written at its own step,
@@ -146,7 +168,7 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
             xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
             cb[k] = k < len ? (int)cp[(int64_t)k << 5] : 0;
         }
-        for (int j0 = 0; j0 < len; j0 += kU) {
+        for (int j0 = 0; j0 < lenU; j0 += kU) {
             float xn[kU];
             int cn[kU];
 #pragma unroll
@@ -156,31 +178,18 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
                 cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
             }
 #pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                const float x = xb[k];
-                const int c = cb[k];
-                const float u = (float)(2 * c - cmax);
-                const float xS = x * S;
-                const float T = fmaf(-u, I, xS);
-                const bool up = T > 0.f;
-                const bool ok = active && (j0 + k < len) && (up ? c < cmax : c > 0) &&
-                                fmaf(fabsf(T), I, x * xS) > I2;
-                if (ok) {
-                    const float s2 = up ? 2.f : -2.f;
-                    I = fmaf(s2, x, I);
-                    S = fmaf(2.f * s2, u, S + 4.f);
-                    I2 = I * I;
-                    cp[(int64_t)(j0 + k) << 5] = (uint8_t)(up ? c + 1 : c - 1);
-                    moved = true;
-                }
-            }
+            for (int k = 0; k < kU; ++k) step(xb[k], cb[k], j0 + k, moved);
 #pragma unroll
             for (int k = 0; k < kU; ++k) {
                 xb[k] = xn[k];
                 cb[k] = cn[k];
             }
         }
-        active = active && moved;
+        // the last, partial batch
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (lenU + k < len) step(xb[k], cb[k], lenU + k, moved);
+        if (!moved) I2 = __int_as_float(0x7f800000);
     }
 
     // bit-planes from the codes (most significant first, 64-bit words)
