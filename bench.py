@@ -12,6 +12,7 @@ Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -31,6 +32,32 @@ from paper_2509_12086_gb300 import synth  # noqa: E402
 
 METRIC = "SAQ encoded vectors/s at d=960 4b/dim, FP32 vs BF16; ingest p50/p99 latency"
 UNIT = "vectors/s"
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per row of one
+# launch of each encode kernel, from `ncu --set full` captures of the 65,536-row
+# case of the default workload (one launch each; profiles/k_proj_tc_split_n65536.md,
+# profiles/k_caq1_n65536.md).  Both kernels stream their rows, so a launch's
+# traffic is proportional to its rows.  A figure is reported only while the
+# kernel's source file is the one that was captured (SHA-1 below).
+NCU_TRAFFIC = {
+    "projection": {"src": "k_tc.cu", "sha1": "8833e5c93d3f8552397c2db070d9ff890bb26e80",
+                   "workload": "c2_d960", "precision": "fp32",
+                   "bytes_per_row": (258.173952e6 + 212.143360e6) / 65536},
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "336b7ac207606ab9096ff4ad2b96f712923b8f1b",
+                             "workload": "c2_d960", "precision": "fp32",
+                             "bytes_per_row": (1981.201e6 + 275.075840e6) / 65536},
+}
+
+
+def traffic_per_launch(kind, workload, precision, rows_per_launch):
+    e = NCU_TRAFFIC.get(kind)
+    if not e or e["workload"] != workload or e["precision"] != precision:
+        return None
+    with open(os.path.join(ROOT, "paper_2509_12086_gb300", "csrc", e["src"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != e["sha1"]:
+            return None
+    return e["bytes_per_row"] * rows_per_launch
 
 
 def peaks():
@@ -158,11 +185,50 @@ def cpu_baseline(w, X_dev, target_s=12.0):
     ns = int(min(fit_rows, max(2000, target_s / max(per, 1e-9))))
     Xs = Xf[:ns]
     t0 = time.perf_counter()
-    O.encode(Xs, mo, rounds=w["rounds"])
+    enc = O.encode(Xs, mo, rounds=w["rounds"])
     dt = time.perf_counter() - t0
     return {"value": ns / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": "%d rows of the workload (oracle fit on %d rows, not timed): "
-                      "FP64 projection + CAQ + factors, %.1f s" % (ns, fit_rows, dt)}, mo
+                      "FP64 projection + CAQ + factors, %.1f s" % (ns, fit_rows, dt)}, mo, enc
+
+
+# Algorithmic lane operations of quantize / adjust / pack (Eq. find_nearest_code,
+# Algorithm 1, factors, bit-planes), per coordinate:
+#   initial code: fma, floor, two clamps; I, |o|^2 and |u|^2 accumulations   7
+#   one trial of a round: o*S, T = o*S - u*I, o*(o*S), |T|*I + o^2*S,
+#     comparison with I^2, range check                                      6
+#   an accepted move: I, S, I^2, the code                                   4
+#   packing: extract and insert one bit per bit-plane                       2 per plane
+ALU_INIT, ALU_TRIAL, ALU_ACCEPT, ALU_PACK = 7, 6, 4, 2
+
+
+def alu_ops_per_vector(enc, mo, rounds):
+    """Lane operations per vector counted from the oracle's accept statistics:
+    a vector-segment runs rounds through its first round without an accept."""
+    ops = 0.0
+    for j, (off, l, b) in enumerate(mo.kept):
+        a = enc.accepts[:, j, :rounds]
+        zero = a == 0
+        ran = np.where(zero.any(axis=1), zero.argmax(axis=1) + 1, rounds)
+        ops += l * (ALU_INIT + ALU_PACK * b) + l * ALU_TRIAL * ran.mean()
+        ops += ALU_ACCEPT * a.sum(axis=1).mean()
+    return ops
+
+
+def tf32_peak(dev, stream):
+    """Measured cuBLAS TF32 GEMM rate (8192^3, FP32 operands), TFLOP/s."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(8192, 8192, device=dev)
+        b = torch.randn(8192, 8192, device=dev)
+        for _ in range(3):
+            torch.mm(a, b)
+        t = time_events(lambda: torch.mm(a, b), 10, stream)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b
+    return 2.0 * 8192 ** 3 / t / 1e12
 
 
 def run_reference(args):
@@ -230,21 +296,40 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     l0 = P.saq_kernel_launch_count()
+    P.saq_kernel_timing(True)
     t_dev = time_events(step, args.steps, stream) * args.steps
     launches = P.saq_kernel_launch_count() - l0
     clocks = clk.stop()
+    # each launch's device time inside the timed steps (events on its own stream)
+    ktimes = P.saq_kernel_times()
+    P.saq_kernel_timing(False)
     torch.cuda.synchronize()
     barrier(world)
     t_max = max_over_ranks(world, t_dev)
     value = n * world * args.steps / t_max
 
-    # per-kernel breakdown of one step, in the encode's own data layout:
-    # projection alone and quantize/adjust/pack alone (serial, no overlap)
+    # kernel times per step from the timed region (the encode overlaps the
+    # projection of one chunk with the quantization of the previous one, so a
+    # launch's duration includes the sharing of the SMs)
+    (ms_p, l_p), (ms_q, l_q) = ktimes["projection"], ktimes["quantize_adjust_pack"]
+    t_proj = ms_p / 1e3 / args.steps
+    t_caq = ms_q / 1e3 / args.steps
+    # the same kernels alone (serial), in the encode's own data layout; the
+    # kernel timer separates k_caq1 from the v_max pass this form adds
     rows = min(n, 262144)
     O_buf, nrm = m.project_interleaved(X[:rows])
     c2, f2 = m.alloc_outputs(rows, dev)
-    t_proj = time_events(lambda: m.project_interleaved(X[:rows]), 3, stream) * n / rows
-    t_caq = time_events(lambda: m.quantize_interleaved(O_buf, nrm, c2, f2), 3, stream) * n / rows
+    m.quantize_interleaved(O_buf, nrm, c2, f2)
+    torch.cuda.synchronize()
+    P.saq_kernel_timing(True)
+    for _ in range(3):
+        m.project_interleaved(X[:rows])
+        m.quantize_interleaved(O_buf, nrm, c2, f2)
+    torch.cuda.synchronize()
+    ka = P.saq_kernel_times()
+    P.saq_kernel_timing(False)
+    t_proj_alone = ka["projection"][0] / 1e3 / 3 * n / rows
+    t_caq_alone = ka["quantize_adjust_pack"][0] / 1e3 / 3 * n / rows
     del O_buf, c2, f2
     plan = m.plan
     dk = m.d_kept
@@ -262,10 +347,23 @@ def run_ours(args):
         proj_roof = {"bound": "tensor", "achieved": flops / t_proj / 1e12, "peak": pkv,
                      "unit": "TFLOP/s", "frac": flops / t_proj / 1e12 / pkv, "traffic": None,
                      "peak_source": "%s bf16 sustained" % pk["source"]}
+        if args.precision == "fp32":
+            # FP32 operands reach the tensor cores as TF32 or as a split into
+            # FP16 pairs (three products here): the fraction of the measured
+            # TF32 GEMM rate is the other yardstick
+            tf = tf32_peak(dev, stream)
+            proj_roof["tf32_peak_measured"] = tf
+            proj_roof["frac_of_tf32"] = flops / t_proj / 1e12 / tf
     caq_bytes = n * (4.0 * dk + m.code_bytes + 4.0 * m.factor_count)
     caq_roof = {"bound": "hbm", "achieved": caq_bytes / t_caq / 1e9, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": caq_bytes / t_caq / 1e9 / pk["hbm_gbs"], "traffic": None,
                 "peak_source": "%s hbm copy" % pk["source"]}
+    # per launch, like `achieved` (algorithmic bytes or flops of one launch's rows)
+    proj_roof["traffic"] = traffic_per_launch("projection", args.workload, args.precision,
+                                              n / max(l_p / args.steps, 1))
+    caq_roof["traffic"] = traffic_per_launch("quantize_adjust_pack", args.workload, args.precision,
+                                             n / max(l_q / args.steps, 1))
+    caq_roof["algorithmic_bytes_per_launch"] = caq_bytes / max(l_q / args.steps, 1)
     if t_proj >= t_caq:
         roof, dom = proj_roof, "projection"
     else:
@@ -310,8 +408,18 @@ def run_ours(args):
         ingest = serving_run(args, dev)
 
     cpu = None
+    alu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_baseline(w, X)
+        cpu, mo, enc = cpu_baseline(w, X)
+        if mo.plan == plan:
+            ops = alu_ops_per_vector(enc, mo, w["rounds"])
+            sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
+            alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+            alu = {"bound": "alu", "kernel": "quantize_adjust_pack",
+                   "ops_per_vector": ops, "achieved": ops * n / t_caq / 1e12, "peak": alu_peak,
+                   "unit": "Tops/s", "frac": ops * n / t_caq / 1e12 / alu_peak,
+                   "peak_source": "152 SMs x 128 lanes x %.0f MHz (one op per lane per clock)" % sm_mhz,
+                   "counted_from": "oracle accept statistics of the cpu_baseline sample"}
 
     if rank == 0:
         cfg = workload_desc(w, args.workload, args.precision, plan, m.code_bytes)
@@ -322,7 +430,12 @@ def run_ours(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": cfg, "roofline": roof,
                "kernels_ms_per_step": {"projection": t_proj * 1e3,
-                                       "quantize_adjust_pack": t_caq * 1e3},
+                                       "quantize_adjust_pack": t_caq * 1e3,
+                                       "launches_per_step": {"projection": l_p / args.steps,
+                                                             "quantize_adjust_pack": l_q / args.steps}},
+               "kernels_ms_per_step_alone": {"projection": t_proj_alone * 1e3,
+                                             "quantize_adjust_pack": t_caq_alone * 1e3},
+               "alu_roofline": alu,
                "other_kernel_roofline": caq_roof if dom == "projection" else proj_roof,
                "step_roofline_vectors_per_s": step_roof,
                "step_roofline_frac": value / world / step_roof,

@@ -324,6 +324,22 @@ saq_status saq_ingest_close(saq_ingest *s);
  * (all threads, all devices).  Diagnostic; never reset. */
 uint64_t saq_kernel_launch_count(void);
 
+/* Kernel timing (diagnostic; no counterpart in the paper).  While enabled,
+ * every kernel the library launches is bracketed by two CUDA events recorded
+ * on its own stream, just before the launch and just after it, so that each
+ * interval is that launch's device time even when streams overlap.
+ * saq_kernel_timing(1) clears the record and starts recording (all threads,
+ * all devices); saq_kernel_timing(0) stops and keeps the record.  saq_kernel_times() waits for the
+ * recorded events and writes, for kind k < kinds, the summed milliseconds
+ * ms[k] and the number of launches launches[k]:
+ *   k = 0  projection (tensor-core or CUDA-core GEMM of the encode),
+ *   k = 1  quantize / adjust / pack (Eq. find_nearest_code, Algorithm 1),
+ *   k = 2  everything else (v_max pass, layout changes, estimator, fit).
+ * kinds must be 1..3; ms and launches are host arrays of `kinds` entries.
+ * SAQ_ERR_INVALID on bad arguments, SAQ_ERR_CUDA if an event failed. */
+saq_status saq_kernel_timing(int enable);
+saq_status saq_kernel_times(double *ms, int64_t *launches, int kinds);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *saq_last_error(void);
 const char *saq_status_string(saq_status s);

@@ -36,6 +36,7 @@ EXPORTS = [
     "saq_encode_noalloc", "saq_model_uses_tensor_cores", "saq_check_device",
     "saq_ingest_open", "saq_ingest_submit", "saq_ingest_poll", "saq_ingest_wait",
     "saq_ingest_get_stats", "saq_ingest_close", "saq_project_ex", "saq_quantize_projected_ex",
+    "saq_kernel_timing", "saq_kernel_times",
 ]
 
 
@@ -107,6 +108,9 @@ def load() -> ctypes.CDLL:
         "saq_last_error": (ctypes.c_char_p, []),
         "saq_status_string": (ctypes.c_char_p, [st]),
         "saq_kernel_launch_count": (ctypes.c_uint64, []),
+        "saq_kernel_timing": (st, [ctypes.c_int]),
+        "saq_kernel_times": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.c_int]),
         "saq_encode_noalloc": (st, [mp, vp, i64, vp, vp, vp]),
         "saq_model_uses_tensor_cores": (i32, [mp]),
         "saq_check_device": (st, [mp, vp]),
@@ -358,6 +362,24 @@ def saq_plan_search(sig2, quota_bits: int, g: int = 64, max_bits: int = 8,
 
 def saq_kernel_launch_count() -> int:
     return int(load().saq_kernel_launch_count())
+
+
+KERNEL_KINDS = ("projection", "quantize_adjust_pack", "other")
+
+
+def saq_kernel_timing(enable: bool) -> None:
+    """Start (clearing the record) or stop (keeping it) per-launch device
+    timing."""
+    _check(load().saq_kernel_timing(1 if enable else 0))
+
+
+def saq_kernel_times() -> dict:
+    """{kind: (summed ms, launches)} of the launches recorded since timing
+    was enabled."""
+    ms = (ctypes.c_double * 3)()
+    ln = (ctypes.c_int64 * 3)()
+    _check(load().saq_kernel_times(ms, ln, 3))
+    return {k: (float(ms[i]), int(ln[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def saq_model_import(blob: bytes) -> Model:

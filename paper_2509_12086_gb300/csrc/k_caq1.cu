@@ -274,8 +274,11 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
     std::stable_sort(t.order, t.order + nk, [&](int a, int b) { return t.s[a].len > t.s[b].len; });
     const int64_t warps = (n + 31) / 32 * nk;
     const int64_t blocks = (warps + 7) / 8;
-    k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, m->dk, nk, t, m->rounds, cs, vmax, codes,
-                                            (int64_t)m->code_bytes, factors, m->nf);
+    {
+        LaunchTimer lt_(kKindQuantize, s);
+        k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, m->dk, nk, t, m->rounds, cs, vmax, codes,
+                                                (int64_t)m->code_bytes, factors, m->nf);
+    }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
@@ -286,7 +289,10 @@ saq_status launch_seg_vmax(const saq_model *m, const float *Oi, int64_t n, float
     const SegCols sc = seg_cols(m);
     if (n <= 0 || sc.nk == 0) return SAQ_OK;
     const int64_t warps = (n + 31) / 32 * sc.nk;
-    k_seg_vmax<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(Oi, n, m->dk, sc, vmax);
+    {
+        LaunchTimer lt_(kKindOther, s);
+        k_seg_vmax<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(Oi, n, m->dk, sc, vmax);
+    }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
@@ -302,12 +308,18 @@ saq_status launch_interleave(const float *O, int64_t ldo, int64_t n, int dk, flo
         for (int64_t g0 = 0; g0 < groups; g0 += 65535) {
             const int64_t gn = std::min<int64_t>(65535, groups - g0);
             dim3 gg((unsigned)((dk + 31) / 32), (unsigned)gn);
-            k_interleave<<<gg, dim3(32, 8), 0, s>>>(O + g0 * 32 * ldo, ldo, n - g0 * 32, dk,
-                                                    Oi + g0 * 32 * (int64_t)dk);
+            {
+                LaunchTimer lt_(kKindOther, s);
+                k_interleave<<<gg, dim3(32, 8), 0, s>>>(O + g0 * 32 * ldo, ldo, n - g0 * 32, dk,
+                                                        Oi + g0 * 32 * (int64_t)dk);
+            }
             note_launches();
         }
     } else {
-        k_interleave<<<grid, dim3(32, 8), 0, s>>>(O, ldo, n, dk, Oi);
+        {
+            LaunchTimer lt_(kKindOther, s);
+            k_interleave<<<grid, dim3(32, 8), 0, s>>>(O, ldo, n, dk, Oi);
+        }
         note_launches();
     }
     SAQ_CUDA_CHECK(cudaGetLastError());

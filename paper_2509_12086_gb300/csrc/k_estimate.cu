@@ -95,12 +95,18 @@ saq_status launch_estimate(const saq_model *m, const uint8_t *codes, const float
         t.s[i] = SegDesc{k.off, k.len, k.bits, k.words, k.fidx, (long long)k.code_off};
     }
     const int64_t cs = (int64_t)m->code_bytes;
-    k_vec_scale<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(codes, cs, factors, m->nf, n, nk, t,
-                                                         prefix_bits, vscale);
+    {
+        LaunchTimer lt_(kKindOther, s);
+        k_vec_scale<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(codes, cs, factors, m->nf, n, nk, t,
+                                                             prefix_bits, vscale);
+    }
     const int64_t warps = n * nq;
-    k_estimate<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(codes, cs, factors, m->nf, n, nk, t,
-                                                           prefix_bits, vscale, Qrot, m->dk, qn2,
-                                                           nq, dist);
+    {
+        LaunchTimer lt_(kKindOther, s);
+        k_estimate<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(codes, cs, factors, m->nf, n, nk, t,
+                                                               prefix_bits, vscale, Qrot, m->dk, qn2,
+                                                               nq, dist);
+    }
     note_launches(2);
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;

@@ -106,8 +106,11 @@ saq_status launch_project_simt(const saq_model *m, const float *X, int64_t n,
         const int64_t rows = n - r0 < (int64_t)kBM * 65535 ? n - r0 : (int64_t)kBM * 65535;
         dim3 grid((unsigned)((rows + kBM - 1) / kBM), (unsigned)((m->dk + kBN - 1) / kBN));
         float *Ob = layout == kInterleaved ? O + r0 * m->dk : O + r0 * ldo;
-        k_project_simt<<<grid, 256, 0, s>>>(X + r0 * m->d, rows, m->d, m->d_mean, m->d_W,
-                                            m->dk, Ob, ldo, layout == kInterleaved ? 1 : 0);
+        {
+            LaunchTimer lt_(kKindProject, s);
+            k_project_simt<<<grid, 256, 0, s>>>(X + r0 * m->d, rows, m->d, m->d_mean, m->d_W,
+                                                m->dk, Ob, ldo, layout == kInterleaved ? 1 : 0);
+        }
         note_launches();
     }
     SAQ_CUDA_CHECK(cudaGetLastError());
@@ -118,7 +121,10 @@ saq_status launch_rownorm2(const saq_model *m, const float *X, int64_t n,
                            float *out, int64_t stride, cudaStream_t s) {
     if (n <= 0) return SAQ_OK;
     const int64_t blocks = (n + 7) / 8;
-    k_rownorm2<<<(unsigned)blocks, 256, 0, s>>>(X, n, m->d, m->d_mean, out, stride);
+    {
+        LaunchTimer lt_(kKindOther, s);
+        k_rownorm2<<<(unsigned)blocks, 256, 0, s>>>(X, n, m->d, m->d_mean, out, stride);
+    }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
@@ -127,7 +133,10 @@ saq_status launch_rownorm2(const saq_model *m, const float *X, int64_t n,
 saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
                                int64_t dstride, int64_t n, cudaStream_t s) {
     if (n <= 0) return SAQ_OK;
-    k_copy_strided<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, sstride, dst, dstride, n);
+    {
+        LaunchTimer lt_(kKindOther, s);
+        k_copy_strided<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, sstride, dst, dstride, n);
+    }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;

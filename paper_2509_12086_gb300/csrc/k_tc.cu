@@ -651,11 +651,14 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
     const int64_t tiles = (n + kBM - 1) / kBM;
     const int64_t blocks = tiles * ex->npass;
     if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
-    k_proj_tc<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(
-        tmx, (const uint8_t *)m->tc.w_hi,
-        (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi), n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
-        m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, vmax, seg_cols(m),
-        ex->err);
+    {
+        LaunchTimer lt_(kKindProject, s);
+        k_proj_tc<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(
+            tmx, (const uint8_t *)m->tc.w_hi,
+            (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi), n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
+            m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, vmax, seg_cols(m),
+            ex->err);
+    }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <atomic>
 #include <limits>
+#include <mutex>
+#include <vector>
 
 #include "saq_internal.h"
 
@@ -30,6 +32,35 @@ void clear_error() { g_last_error.clear(); }
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+namespace {
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+};
+std::atomic<int> g_timing{0};
+std::mutex g_timing_mu;
+std::vector<TimedLaunch> g_timed;
+}  // namespace
+
+LaunchTimer::LaunchTimer(int k, cudaStream_t st) : kind(k), s(st) {
+    if (!g_timing.load(std::memory_order_relaxed)) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        a = nullptr;
+    }
+}
+LaunchTimer::~LaunchTimer() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(b, s) != cudaSuccess) {
+        if (b) cudaEventDestroy(b);
+        cudaEventDestroy(a);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timed.push_back(TimedLaunch{kind, a, b});
+}
 
 // ------------------------------------------------------------------------
 // Quantization plan search, Sec. 4.2 Algorithm 2.
@@ -258,6 +289,42 @@ void saq_params_init(saq_params *p) {
 const char *saq_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t saq_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+saq_status saq_kernel_timing(int enable) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (!enable) {  // stop; the record stays readable
+        g_timing.store(0);
+        return SAQ_OK;
+    }
+    for (const TimedLaunch &t : g_timed) {
+        cudaEventSynchronize(t.b);
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    g_timed.clear();
+    g_timing.store(1);
+    return SAQ_OK;
+}
+
+saq_status saq_kernel_times(double *ms, int64_t *launches, int kinds) {
+    if (!ms || !launches || kinds < 1 || kinds > kKindCount)
+        return set_error(SAQ_ERR_INVALID, "saq_kernel_times: need host arrays of 1..%d kinds", kKindCount);
+    for (int k = 0; k < kinds; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (const TimedLaunch &t : g_timed) {
+        float e = 0.f;
+        SAQ_CUDA_CHECK(cudaEventSynchronize(t.b));
+        SAQ_CUDA_CHECK(cudaEventElapsedTime(&e, t.a, t.b));
+        if (t.kind < kinds) {
+            ms[t.kind] += e;
+            launches[t.kind] += 1;
+        }
+    }
+    return SAQ_OK;
+}
 
 saq_status saq_plan_search(const double *sig2, int32_t d, int32_t g, int64_t quota_bits,
                            int32_t max_bits, double tie_frac, saq_segment *out, int32_t cap,

@@ -17,6 +17,20 @@ namespace saq {
 saq_status set_error(saq_status s, const char *fmt, ...);
 // Count `k` kernel launches (saq_kernel_launch_count).
 void note_launches(int k = 1);
+
+// Optional per-launch device timing (saq_kernel_timing): a scope that records
+// a CUDA event on `s` when it is opened (just before a launch) and another
+// when it closes (just after it).
+enum KernelKind { kKindProject = 0, kKindQuantize = 1, kKindOther = 2, kKindCount = 3 };
+struct LaunchTimer {
+    LaunchTimer(int kind, cudaStream_t s);
+    ~LaunchTimer();
+    LaunchTimer(const LaunchTimer &) = delete;
+    LaunchTimer &operator=(const LaunchTimer &) = delete;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+};
 void clear_error();
 
 #define SAQ_CUDA_CHECK(call)                                                   \
