@@ -174,6 +174,7 @@ class Model:
     plan: List[Tuple[int, int, int]]      # all segments, PCA dimension order
     sig2: np.ndarray = None               # (d,) PCA eigenvalues
     kept: List[Tuple[int, int, int]] = field(default_factory=list)  # (off, len, bits)
+    V: np.ndarray = None                  # (d, d) PCA eigenvectors (columns), if known
 
     def __post_init__(self):
         if not self.kept:
@@ -219,7 +220,7 @@ def fit(X: np.ndarray, avg_bits: float, g: int = 64, max_bits: int = 8,
     d = X.shape[1]
     plan = plan_dp(sig2, int(round(avg_bits * d)), g, max_bits, tie_frac)
     W = build_matrix(V, plan.segments, seed)
-    return Model(d=d, mean=c, W=W, plan=plan.segments, sig2=sig2)
+    return Model(d=d, mean=c, W=W, plan=plan.segments, sig2=sig2, V=V)
 
 
 # --------------------------------------------------------------------------
@@ -375,6 +376,74 @@ def estimate(model: Model, codes: np.ndarray, factors: np.ndarray,
         scale = np.where(nrm > 0, nrm / (un * np.where(cs != 0, cs, 1.0)), 0.0)
         est += (qr[:, off:off + l] @ u.T) * scale[None, :]
     return factors[None, :, 0] + qn2[:, None] - 2.0 * est
+
+
+# --------------------------------------------------------------------------
+# Multi-stage estimation (Sec. 4.3)
+# --------------------------------------------------------------------------
+def kept_basis(model: Model) -> np.ndarray:
+    """(d_kept, d): the PCA directions v_i^T of the kept dimensions, plan
+    order (the rows W_s mixes with the segment rotation R_s)."""
+    rows = [model.V[:, s:s + l].T for s, l, b in model.plan if b > 0]
+    return np.concatenate(rows, axis=0) if rows else np.zeros((0, model.d))
+
+
+def segment_sigma(model: Model, Q: np.ndarray) -> np.ndarray:
+    """(nq, k): sigma_Seg(q) of every kept segment, Sec. 4.3:
+        sigma_Seg^2 = sum_{i in Seg} q[i]^2 sigma_i^2
+    with q in the PCA coordinates, q[i] = v_i^T (q_r - c), and sigma_i^2 the
+    variance of PCA dimension i over the dataset.  It is the variance of
+    <o_seg, q_seg> over the data vectors (the segment rotation R_s does not
+    change an inner product)."""
+    Qp = (Q.astype(np.float64) - model.mean) @ model.V      # (nq, d) PCA coordinates
+    out = np.zeros((Q.shape[0], len(model.kept)))
+    j = 0
+    for s, l, b in model.plan:
+        if b == 0:
+            continue
+        out[:, j] = np.sqrt(np.sum(Qp[:, s:s + l] ** 2 * model.sig2[None, s:s + l], axis=1))
+        j += 1
+    return out
+
+
+def segment_estimates(model: Model, codes: np.ndarray, factors: np.ndarray,
+                      Q: np.ndarray) -> np.ndarray:
+    """(nq, n, k): est_s = |o_s| <u_s, q_s> / (|u_s| cos_s) per kept segment
+    (the per-segment term of the Sec. 3.2 estimator)."""
+    qr = (Q.astype(np.float64) - model.mean) @ model.W.T
+    out = np.zeros((Q.shape[0], codes.shape[0], len(model.kept)))
+    for j, (off, l, b) in enumerate(model.kept):
+        u = 2.0 * codes[:, off:off + l].astype(np.float64) - (2.0 ** b - 1.0)
+        un = np.sqrt(np.sum(u * u, axis=1))
+        nrm = factors[:, 1 + 2 * j]
+        cs = factors[:, 2 + 2 * j]
+        scale = np.where(nrm > 0, nrm / (un * np.where(cs != 0, cs, 1.0)), 0.0)
+        out[:, :, j] = (qr[:, off:off + l] @ u.T) * scale[None, :]
+    return out
+
+
+def estimate_staged(model: Model, codes: np.ndarray, factors: np.ndarray,
+                    Q: np.ndarray, m_conf: float) -> np.ndarray:
+    """(nq, n, k + 1) multi-stage lower bounds of the squared distance,
+    Sec. 4.3: stages take the kept segments in plan order (decreasing
+    variance).  After t stages the first t segments contribute their
+    estimates and each remaining one its Chebyshev bound m * sigma_Seg(q)
+    (|<o_seg, q_seg>| < m sigma_Seg with probability >= 1 - 1/m^2):
+        lb_t = |o_r - c|^2 + |q_r - c|^2
+               - 2 (sum_{s < t} est_s + m sum_{s >= t} sigma_s(q)).
+    lb_k is the estimate of Sec. 3.2; dropped segments contribute nothing,
+    as in that estimate."""
+    est = segment_estimates(model, codes, factors, Q)
+    sig = segment_sigma(model, Q)
+    Qc = Q.astype(np.float64) - model.mean
+    base = factors[None, :, 0] + np.einsum("ij,ij->i", Qc, Qc)[:, None]
+    k = len(model.kept)
+    out = np.zeros((Q.shape[0], codes.shape[0], k + 1))
+    for t in range(k + 1):
+        done = est[:, :, :t].sum(axis=2)
+        rest = m_conf * sig[:, t:].sum(axis=1)
+        out[:, :, t] = base - 2.0 * (done + rest[:, None])
+    return out
 
 
 def exact_dist(X: np.ndarray, Q: np.ndarray) -> np.ndarray:

@@ -473,3 +473,72 @@ def test_progressive_prefix_is_a_valid_estimator():
     p1 = O.relative_error(O.estimate(m, e.codes, e.factors, Qm, prefix_bits=1), ex).mean()
     assert full < p4 < p1
     assert p1 < 0.5
+
+
+# ---------------------------------------------------- multi-stage estimation
+def test_segment_sigma_is_the_variance_of_the_segment_inner_product():
+    """Sec. 4.3: sigma_Seg^2 = sum_{i in Seg} q[i]^2 sigma_i^2 is the
+    variance, over the data vectors, of <o_seg, q_seg>.  Computed here the
+    other way round: the empirical (1/N) variance over the fitted rows of
+    <W_s (x - c), W_s (q - c)>, through the rotated matrix W and the data."""
+    X, _, _ = _power_law(5000, 128, 0.8, seed=21)
+    m = O.fit(X, 3.0)
+    rng = np.random.default_rng(22)
+    Qm = X[rng.choice(5000, 30, replace=False)] + 0.1 * rng.standard_normal((30, 128))
+    sig = O.segment_sigma(m, Qm)
+    Oproj, _ = O.project(X, m)
+    Qr, _ = O.project(Qm, m)
+    for j, (off, l, b) in enumerate(m.kept):
+        ip = Oproj[:, off:off + l] @ Qr[:, off:off + l].T          # (N, nq)
+        var = ip.var(axis=0)                                        # 1/N, as the PCA
+        assert np.allclose(sig[:, j] ** 2, var, rtol=1e-9, atol=1e-12)
+
+
+def test_chebyshev_bound_holds_per_segment():
+    """Sec. 4.3: |<o_seg, q_seg>| >= m sigma_Seg with probability <= 1/m^2
+    (Chebyshev, the inner product has mean 0 over centred data).  On the
+    fitted rows the empirical frequency obeys the bound for every segment
+    and every m; for near-normal values it is far below it."""
+    X, _, _ = _power_law(6000, 96, 1.0, seed=23)
+    m = O.fit(X, 2.0)
+    Qm = X[:40]
+    sig = O.segment_sigma(m, Qm)
+    Oproj, _ = O.project(X, m)
+    Qr, _ = O.project(Qm, m)
+    for j, (off, l, b) in enumerate(m.kept):
+        ip = np.abs(Oproj[:, off:off + l] @ Qr[:, off:off + l].T)
+        for mc in (1.5, 2.0, 3.0):
+            freq = np.mean(ip >= mc * sig[None, :, j])
+            assert freq <= 1.0 / mc ** 2
+        assert np.mean(ip >= 2.0 * sig[None, :, j]) < 0.1
+
+
+def test_staged_estimate_ends_at_the_estimate_and_starts_at_the_prior_bound():
+    """Sec. 4.3 multi-stage estimator: after all kept segments it is the
+    Sec. 3.2 estimate; before any, |x - c|^2 + |q - c|^2 - 2 m sum_s
+    sigma_s(q); each stage swaps one Chebyshev bound for one estimate, so
+    the step t -> t+1 is 2 (m sigma_t - est_t), and m = 0 keeps only the
+    estimated stages."""
+    X, _, _ = _power_law(3000, 128, 0.8, seed=24)
+    m = O.fit(X, 4.0)
+    e = O.encode(X[:50], m, rounds=6)
+    Qm = X[-20:]
+    k = len(m.kept)
+    st = O.estimate_staged(m, e.codes, e.factors, Qm, 2.0)
+    assert st.shape == (20, 50, k + 1)
+    full = O.estimate(m, e.codes, e.factors, Qm)
+    assert np.allclose(st[:, :, k], full, rtol=1e-12, atol=1e-9)
+    Qc = Qm - m.mean
+    base = e.factors[None, :, 0] + np.sum(Qc * Qc, axis=1)[:, None]
+    sig = O.segment_sigma(m, Qm)
+    assert np.allclose(st[:, :, 0], base - 4.0 * sig.sum(axis=1)[:, None], rtol=1e-12)
+    est = O.segment_estimates(m, e.codes, e.factors, Qm)
+    for t in range(k):
+        step = st[:, :, t + 1] - st[:, :, t]
+        assert np.allclose(step, 2.0 * (2.0 * sig[:, t][:, None] - est[:, :, t]), rtol=1e-9,
+                           atol=1e-9)
+    # the stage-t bound is a lower bound of the exact distance for most pairs
+    ex = O.exact_dist(X[:50], Qm)
+    assert np.mean(st[:, :, 0] <= ex) >= 0.75
+    st0 = O.estimate_staged(m, e.codes, e.factors, Qm, 0.0)
+    assert np.allclose(st0[:, :, 0], base, rtol=1e-12)
