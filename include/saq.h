@@ -240,8 +240,10 @@ saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
                              void *stream);
 
 /*
- * Serialise a model (mean, plan, W, sigma^2, rounds, precision) into a
- * versioned little-endian blob.  With buf == NULL, *len receives the size.
+ * Serialise a model (mean, plan, W, sigma^2, rounds, precision and, when
+ * the model carries one, the PCA basis of saq_model_set_basis) into a
+ * versioned little-endian blob (version 2; import also reads version 1,
+ * which has no basis).  With buf == NULL, *len receives the size.
  * Otherwise *len is the capacity of buf and receives the bytes written.
  */
 saq_status saq_model_export(const saq_model *m, void *buf, size_t *len);
@@ -323,6 +325,37 @@ saq_status saq_ingest_close(saq_ingest *s);
 /* Number of CUDA kernels the library has launched in this process so far
  * (all threads, all devices).  Diagnostic; never reset. */
 uint64_t saq_kernel_launch_count(void);
+
+/* Multi-stage distance estimation (Sec. 4.3).  The kept segments are taken
+ * in plan order, i.e. by decreasing PCA variance.  After t stages the first
+ * t segments contribute their estimates est_s (as in saq_estimate_dist) and
+ * every remaining one its Chebyshev bound m * sigma_Seg(q), where
+ *   sigma_Seg(q)^2 = sum_{i in Seg} sigma_i^2 (v_i . (q_r - c))^2
+ * is the variance of <o_seg, q_seg> over the data (v_i, sigma_i^2: PCA
+ * direction and variance of dimension i), so |<o_seg, q_seg>| < m sigma_Seg
+ * with probability >= 1 - 1/m^2:
+ *   bounds[(q*n + v)*(k+1) + t] = |o_r - c|^2 + |q_r - c|^2
+ *                                 - 2 (sum_{s<t} est_s + m sum_{s>=t} sigma_s(q)),
+ * t = 0 .. k (k = kept segments).  t = k equals saq_estimate_dist; dropped
+ * segments contribute nothing, as there.  A search prunes vector v for
+ * query q as soon as a stage's bound exceeds its current best distance.
+ * codes_dev/factors_dev: n rows as written by saq_encode; Q_dev: nq x d
+ * FP32 row-major; bounds_dev: nq x n x (k+1) FP32, caller-owned.  m_conf
+ * (the paper's m) must be finite and >= 0.  The model must carry the PCA
+ * basis: saq_fit records it; a model built by saq_model_create needs
+ * saq_model_set_basis, else SAQ_ERR_UNSUPPORTED.  Asynchronous on `stream`. */
+saq_status saq_estimate_staged(const saq_model *m, const uint8_t *codes_dev,
+                               const float *factors_dev, int64_t n, const float *Q_dev, int64_t nq,
+                               float m_conf, float *bounds_dev, void *stream);
+
+/* The PCA directions of the kept dimensions (Sec. 4.1), for the bounds of
+ * saq_estimate_staged: Vt is d_kept x d row-major FP64, row r = v_i^T for
+ * the r-th kept dimension in plan order (i = start of its segment + offset),
+ * i.e. W = blockdiag(R_s) Vt.  Copied; exported with the model.
+ * SAQ_ERR_INVALID on NULL or non-finite input.  saq_model_has_basis
+ * returns 1 if the model carries one. */
+saq_status saq_model_set_basis(saq_model *m, const double *Vt);
+int32_t saq_model_has_basis(const saq_model *m);
 
 /* Kernel timing (diagnostic; no counterpart in the paper).  While enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded

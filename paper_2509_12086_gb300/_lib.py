@@ -36,7 +36,8 @@ EXPORTS = [
     "saq_encode_noalloc", "saq_model_uses_tensor_cores", "saq_check_device",
     "saq_ingest_open", "saq_ingest_submit", "saq_ingest_poll", "saq_ingest_wait",
     "saq_ingest_get_stats", "saq_ingest_close", "saq_project_ex", "saq_quantize_projected_ex",
-    "saq_kernel_timing", "saq_kernel_times",
+    "saq_kernel_timing", "saq_kernel_times", "saq_estimate_staged", "saq_model_set_basis",
+    "saq_model_has_basis",
 ]
 
 
@@ -109,6 +110,9 @@ def load() -> ctypes.CDLL:
         "saq_status_string": (ctypes.c_char_p, [st]),
         "saq_kernel_launch_count": (ctypes.c_uint64, []),
         "saq_kernel_timing": (st, [ctypes.c_int]),
+        "saq_estimate_staged": (st, [mp, vp, vp, i64, vp, i64, ctypes.c_float, vp, vp]),
+        "saq_model_set_basis": (st, [mp, ctypes.POINTER(ctypes.c_double)]),
+        "saq_model_has_basis": (ctypes.c_int32, [mp]),
         "saq_kernel_times": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.c_int]),
         "saq_encode_noalloc": (st, [mp, vp, i64, vp, vp, vp]),
@@ -311,6 +315,29 @@ class Model:
                                         _stream(stream)))
         return dist
 
+    def estimate_staged(self, codes: torch.Tensor, factors: torch.Tensor, Q: torch.Tensor,
+                        m_conf: float = 2.0, stream=None) -> torch.Tensor:
+        """Sec. 4.3 multi-stage lower bounds, (nq, n, kept segments + 1)."""
+        n, nq = factors.shape[0], Q.shape[0]
+        if codes.shape[1] != self.code_bytes or not codes.is_contiguous():
+            full = torch.zeros((n, max(self.code_bytes, 1)), dtype=torch.uint8, device=codes.device)
+            full[:, :self.code_bytes] = codes
+            codes = full
+        k = self.factor_count // 2
+        out = torch.empty((nq, n, k + 1), dtype=torch.float32, device=Q.device)
+        _check(load().saq_estimate_staged(self._h, _dptr(codes), _dptr(factors.contiguous()), n,
+                                          _dptr(Q.contiguous()), nq, float(m_conf), _dptr(out),
+                                          _stream(stream)))
+        return out
+
+    def set_basis(self, Vt) -> None:
+        Vt = _f64(Vt)
+        _check(load().saq_model_set_basis(self._h, Vt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    @property
+    def has_basis(self) -> bool:
+        return bool(load().saq_model_has_basis(self._h))
+
     def export(self) -> bytes:
         lib = load()
         ln = ctypes.c_size_t(0)
@@ -331,7 +358,7 @@ def saq_fit(X: torch.Tensor, avg_bits=4.0, max_bits=8, rounds=6, seg_granularity
 
 
 def saq_model_create(d: int, mean, W, plan: Sequence[Tuple[int, int, int]], sig2=None,
-                     rounds=6, precision="fp32") -> Model:
+                     rounds=6, precision="fp32", basis=None) -> Model:
     mean = _f64(mean)
     W = _f64(W) if W is not None else np.zeros((0, d))
     segs = (saq_segment * len(plan))(*[saq_segment(int(s), int(l), int(b)) for s, l, b in plan])
@@ -342,7 +369,10 @@ def saq_model_create(d: int, mean, W, plan: Sequence[Tuple[int, int, int]], sig2
     _check(load().saq_model_create(d, mean.ctypes.data_as(pd), W.ctypes.data_as(pd), segs,
                                    len(plan), s2.ctypes.data_as(pd) if s2 is not None else None,
                                    ctypes.byref(p), ctypes.byref(h)))
-    return Model(h)
+    m = Model(h)
+    if basis is not None:
+        m.set_basis(basis)
+    return m
 
 
 def saq_plan_search(sig2, quota_bits: int, g: int = 64, max_bits: int = 8,

@@ -312,6 +312,22 @@ extern "C" saq_status saq_fit(const float *X_dev, int64_t n, int32_t d, const sa
             ++kidx;
         }
     }
-    return saq_model_create(d, mean.data(), W.data(), plan.data(), (int32_t)plan.size(),
-                            sig2.data(), p, out);
+    st = saq_model_create(d, mean.data(), W.data(), plan.data(), (int32_t)plan.size(),
+                          sig2.data(), p, out);
+    if (st != SAQ_OK || dk == 0) return st;
+    // the PCA directions of the kept dimensions, for the Sec. 4.3 bounds
+    std::vector<double> Vt((size_t)(dk * d));
+    int64_t row = 0;
+    for (auto &sg : plan) {
+        if (sg.bits == 0) continue;
+        for (int r = 0; r < sg.len; ++r, ++row)
+            std::copy(&Vs[(size_t)(sg.start + r) * d], &Vs[(size_t)(sg.start + r) * d] + d,
+                      &Vt[(size_t)row * d]);
+    }
+    st = saq_model_set_basis(*out, Vt.data());
+    if (st != SAQ_OK) {
+        saq_model_free(*out);
+        *out = nullptr;
+    }
+    return st;
 }

@@ -1,6 +1,7 @@
 // saq_encode.cu -- C-ABI entry points of the encode hot path and of the
 // estimator: argument checks, scratch management and kernel sequencing.
 #include <algorithm>
+#include <cmath>
 
 #include "saq_internal.h"
 
@@ -407,6 +408,50 @@ saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
     cudaFreeAsync(qrot, s);
     cudaFreeAsync(qn2, s);
     cudaFreeAsync(vs, s);
+    return st;
+}
+
+saq_status saq_estimate_staged(const saq_model *m, const uint8_t *codes_dev,
+                               const float *factors_dev, int64_t n, const float *Q_dev, int64_t nq,
+                               float m_conf, float *bounds_dev, void *stream) {
+    clear_error();
+    if (!m) return set_error(SAQ_ERR_INVALID, "model is NULL");
+    if (n < 0 || nq < 0) return set_error(SAQ_ERR_INVALID, "negative size");
+    if (!(m_conf >= 0.f) || !std::isfinite(m_conf))
+        return set_error(SAQ_ERR_INVALID, "m must be finite and >= 0");
+    if (m->Vt.empty() || !m->d_B)
+        return set_error(SAQ_ERR_UNSUPPORTED,
+                         "the model carries no PCA basis (saq_fit sets it; see saq_model_set_basis)");
+    if (n == 0 || nq == 0) return SAQ_OK;
+    if (n * nq > ((int64_t)1 << 33)) return set_error(SAQ_ERR_UNSUPPORTED, "n * nq too large");
+    if (!factors_dev || !Q_dev || !bounds_dev || (m->code_bytes > 0 && !codes_dev))
+        return set_error(SAQ_ERR_INVALID, "NULL buffer");
+    if (!aligned16(codes_dev) || !aligned16(factors_dev) || !aligned16(Q_dev))
+        return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    saq_status st = check_device(m);
+    if (st != SAQ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nk = std::max<size_t>(1, m->kept.size());
+    float *qrot = nullptr, *qn2 = nullptr, *vs = nullptr, *qsig = nullptr;
+    const size_t bq = sizeof(float) * (size_t)nq * std::max(1, m->dk);
+    if (cudaMallocAsync((void **)&qrot, bq, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&qn2, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&vs, sizeof(float) * (size_t)n * nk, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&qsig, sizeof(float) * (size_t)nq * nk, s) != cudaSuccess) {
+        if (qrot) cudaFreeAsync(qrot, s);
+        if (qn2) cudaFreeAsync(qn2, s);
+        if (vs) cudaFreeAsync(vs, s);
+        return set_error(SAQ_ERR_OOM, "scratch allocation failed");
+    }
+    st = launch_project_simt(m, Q_dev, nq, qrot, m->dk, kRowMajor, s);
+    if (st == SAQ_OK) st = launch_rownorm2(m, Q_dev, nq, qn2, 1, s);
+    if (st == SAQ_OK)
+        st = launch_estimate_staged(m, codes_dev, factors_dev, n, Q_dev, qrot, qn2, nq, m_conf, vs,
+                                    qsig, bounds_dev, s);
+    cudaFreeAsync(qrot, s);
+    cudaFreeAsync(qn2, s);
+    cudaFreeAsync(vs, s);
+    cudaFreeAsync(qsig, s);
     return st;
 }
 

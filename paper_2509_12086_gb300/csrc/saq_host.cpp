@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <limits>
 #include <mutex>
 #include <vector>
@@ -198,6 +199,8 @@ void model_release_device(saq_model *m) {
     if (!m) return;
     cudaFree(m->d_mean);
     cudaFree(m->d_W);
+    cudaFree(m->d_B);
+    m->d_B = nullptr;
     tc_release(m);
     for (int i = 0; i < 2; ++i) {
         if (m->pipe_s[i]) cudaStreamDestroy(m->pipe_s[i]);
@@ -251,6 +254,24 @@ saq_status model_finalize(saq_model *m) {
         if (st != SAQ_OK) return st;
         SAQ_CUDA_CHECK(cudaDeviceSynchronize());
     }
+    return SAQ_OK;
+}
+
+saq_status model_upload_basis(saq_model *m) {
+    cudaFree(m->d_B);
+    m->d_B = nullptr;
+    if (m->Vt.empty() || m->dk == 0) return SAQ_OK;
+    // row i of the kept dimensions: sigma_i v_i^T, sigma_i of its PCA dimension
+    std::vector<float> b(m->Vt.size());
+    int row = 0;
+    for (const saq::KeptSeg &k : m->kept)
+        for (int r = 0; r < k.len; ++r, ++row) {
+            const double sg = sqrt(std::max(0.0, m->sig2[(size_t)(k.start + r)]));
+            for (int j = 0; j < m->d; ++j)
+                b[(size_t)row * m->d + j] = (float)(sg * m->Vt[(size_t)row * m->d + j]);
+        }
+    SAQ_CUDA_CHECK(cudaMalloc(&m->d_B, sizeof(float) * b.size()));
+    SAQ_CUDA_CHECK(cudaMemcpy(m->d_B, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice));
     return SAQ_OK;
 }
 
@@ -431,6 +452,17 @@ saq_status saq_model_get_variances(const saq_model *m, double *out) {
     return SAQ_OK;
 }
 
+saq_status saq_model_set_basis(saq_model *m, const double *Vt) {
+    clear_error();
+    if (!m || !Vt) return set_error(SAQ_ERR_INVALID, "NULL argument");
+    for (int64_t i = 0; i < (int64_t)m->dk * m->d; ++i)
+        if (!std::isfinite(Vt[i])) return set_error(SAQ_ERR_INVALID, "basis has a non-finite entry");
+    m->Vt.assign(Vt, Vt + (int64_t)m->dk * m->d);
+    return model_upload_basis(m);
+}
+
+int32_t saq_model_has_basis(const saq_model *m) { return m && !m->Vt.empty() ? 1 : 0; }
+
 saq_status saq_model_set_rounds(saq_model *m, int32_t rounds) {
     if (!m || rounds < 0 || rounds > 1000)
         return set_error(SAQ_ERR_INVALID, "bad model or rounds");
@@ -453,15 +485,16 @@ saq_status saq_model_set_precision(saq_model *m, int32_t precision) {
     return SAQ_OK;
 }
 
-// Blob: "SAQM" u32 version=1, i32 d, i32 nseg, i32 rounds, i32 precision,
+// Blob: "SAQM" u32 version, i32 d, i32 nseg, i32 rounds, i32 precision,
 // nseg x (i32 start, i32 len, i32 bits), d x f64 mean, d x f64 sig2,
-// dk x d x f64 W.  Little-endian (host order on every supported host).
-static const uint32_t kVersion = 1;
+// dk x d x f64 W; version 2 adds i32 has_basis and, if set, dk x d x f64 Vt.
+// Little-endian (host order on every supported host).  Import reads 1 and 2.
+static const uint32_t kVersion = 2;
 
 saq_status saq_model_export(const saq_model *m, void *buf, size_t *len) {
     if (!m || !len) return set_error(SAQ_ERR_INVALID, "NULL argument");
     const size_t need = 4 + 4 + 4 * 4 + m->plan.size() * 12 + (size_t)m->d * 16 +
-                        m->W.size() * 8;
+                        m->W.size() * 8 + 4 + m->Vt.size() * 8;
     if (!buf) { *len = need; return SAQ_OK; }
     if (*len < need) return set_error(SAQ_ERR_INVALID, "buffer too small (%zu < %zu)", *len, need);
     uint8_t *p = (uint8_t *)buf;
@@ -477,6 +510,9 @@ saq_status saq_model_export(const saq_model *m, void *buf, size_t *len) {
     put(m->mean.data(), (size_t)m->d * 8);
     put(m->sig2.data(), (size_t)m->d * 8);
     put(m->W.data(), m->W.size() * 8);
+    const int32_t hb = m->Vt.empty() ? 0 : 1;
+    put(&hb, 4);
+    if (hb) put(m->Vt.data(), m->Vt.size() * 8);
     *len = need;
     return SAQ_OK;
 }
@@ -489,7 +525,7 @@ saq_status saq_model_import(const void *buf, size_t len, saq_model **out) {
         return set_error(SAQ_ERR_INVALID, "not a model blob");
     uint32_t ver;
     memcpy(&ver, p + 4, 4);
-    if (ver != kVersion) return set_error(SAQ_ERR_INVALID, "blob version %u unsupported", ver);
+    if (ver != 1 && ver != 2) return set_error(SAQ_ERR_INVALID, "blob version %u unsupported", ver);
     int32_t hdr[4];
     memcpy(hdr, p + 8, 16);
     const int32_t d = hdr[0], nseg = hdr[1];
@@ -515,11 +551,32 @@ saq_status saq_model_import(const void *buf, size_t len, saq_model **out) {
     memcpy(sig2.data(), p + at, (size_t)d * 8);
     at += (size_t)d * 8;
     memcpy(W.data(), p + at, W.size() * 8);
+    at += W.size() * 8;
+    std::vector<double> Vt;
+    if (ver >= 2) {
+        if (len < at + 4) return set_error(SAQ_ERR_INVALID, "truncated blob");
+        int32_t hb = 0;
+        memcpy(&hb, p + at, 4);
+        at += 4;
+        if (hb) {
+            if (len < at + W.size() * 8) return set_error(SAQ_ERR_INVALID, "truncated blob (basis)");
+            Vt.resize(W.size());
+            memcpy(Vt.data(), p + at, Vt.size() * 8);
+        }
+    }
     saq_params prm;
     saq_params_init(&prm);
     prm.rounds = hdr[2];
     prm.precision = hdr[3];
-    return saq_model_create(d, mean.data(), W.data(), plan.data(), nseg, sig2.data(), &prm, out);
+    st = saq_model_create(d, mean.data(), W.data(), plan.data(), nseg, sig2.data(), &prm, out);
+    if (st == SAQ_OK && !Vt.empty()) {
+        st = saq_model_set_basis(*out, Vt.data());
+        if (st != SAQ_OK) {
+            saq_model_free(*out);
+            *out = nullptr;
+        }
+    }
+    return st;
 }
 
 }  // extern "C"

@@ -85,11 +85,13 @@ struct saq_model {
     std::vector<double> mean;             // d
     std::vector<double> W;                // dk x d row-major
     std::vector<double> sig2;             // d (zeros if unknown)
+    std::vector<double> Vt;               // dk x d PCA directions of the kept dims (empty if unknown)
     size_t code_bytes = 0;
     int32_t nf = 1;                       // factors per vector
     // device copies
     float *d_mean = nullptr;              // d
     float *d_W = nullptr;                 // dk x d FP32 row-major
+    float *d_B = nullptr;                 // dk x d FP32: row i = sigma_i v_i^T (if Vt is known)
     saq::TcOperands tc;
     // two library streams that overlap the projection of one chunk with the
     // quantization of the previous one (created on first use)
@@ -111,6 +113,7 @@ int plan_search(const double *sig2, int D, int g, int64_t quota_bits,
 void philox_gaussian(uint64_t seed, uint64_t stream_id, double *out, size_t n);
 
 saq_status model_finalize(saq_model *m);  // derive kept segs, upload
+saq_status model_upload_basis(saq_model *m);  // d_B from Vt and sig2
 saq_status model_build_tc(saq_model *m, int precision, cudaStream_t s);
 void model_release_device(saq_model *m);
 
@@ -165,6 +168,10 @@ saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, in
 saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
                        float *factors, void *scratch, int64_t rows, cudaStream_t s);
 // Estimator.
+saq_status launch_estimate_staged(const saq_model *m, const uint8_t *codes, const float *factors,
+                                  int64_t n, const float *Q, const float *Qrot, const float *qn2,
+                                  int64_t nq, float m_conf, float *vscale, float *qsig,
+                                  float *bounds, cudaStream_t s);
 saq_status launch_estimate(const saq_model *m, const uint8_t *codes,
                            const float *factors, int64_t n, const float *Qrot,
                            const float *qn2, int64_t nq, int prefix_bits,

@@ -320,3 +320,40 @@ def test_interleaved_halves_equal_encode(c1, prec):
     Oi, nrm = m.project_interleaved(Xd)
     c, f = m.quantize_interleaved(Oi, nrm)
     assert torch.equal(c, ref_c) and torch.equal(f, ref_f)
+
+
+def test_c1_staged_estimator_parity(c1):
+    """Sec. 4.3 multi-stage bounds: the library on the oracle's codes against
+    the oracle (FP32 arithmetic only), the last stage against the library's
+    own estimate, the basis through export/import and through saq_fit, and
+    the error for a model without a basis."""
+    X, Qm, mo, eo = c1
+    m = P.saq_model_create(mo.d, mo.mean, mo.W, mo.plan, mo.sig2, basis=O.kept_basis(mo))
+    assert m.has_basis
+    codes_o = torch.from_numpy(O.pack(eo.codes, mo)).cuda()
+    fac_o = torch.from_numpy(eo.factors.astype(np.float32)).cuda()
+    Qt = torch.from_numpy(Qm).cuda()
+    k = len(mo.kept)
+    for mc in (0.0, 1.0, 3.0):
+        bl = m.estimate_staged(codes_o, fac_o, Qt, mc).cpu().numpy().astype(np.float64)
+        bo = O.estimate_staged(mo, eo.codes, eo.factors, Qm, mc)
+        assert bl.shape == bo.shape == (Qm.shape[0], X.shape[0], k + 1)
+        assert np.max(np.abs(bl - bo)) / np.abs(bo).max() < 1e-5, mc
+    dl = m.estimate_dist(codes_o, fac_o, Qt).cpu().numpy()
+    assert np.max(np.abs(bl[:, :, k] - dl)) / np.abs(dl).max() < 1e-6
+    m2 = P.saq_model_import(m.export())
+    assert m2.has_basis
+    b2 = m2.estimate_staged(codes_o, fac_o, Qt, 3.0).cpu().numpy()
+    assert np.array_equal(b2, bl.astype(np.float32))
+    # saq_fit records the basis; its last stage is its own estimate
+    mf = P.saq_fit(torch.from_numpy(X).cuda(), avg_bits=4.0)
+    assert mf.has_basis
+    cf, ff = mf.encode(torch.from_numpy(X).cuda())
+    bf = mf.estimate_staged(cf, ff, Qt, 2.0).cpu().numpy()
+    df = mf.estimate_dist(cf, ff, Qt).cpu().numpy()
+    assert np.max(np.abs(bf[:, :, -1] - df)) / np.abs(df).max() < 1e-6
+    # without a basis the bounds are unavailable
+    m0 = lib_model(mo)
+    assert not m0.has_basis
+    with pytest.raises(P.SaqError):
+        m0.estimate_staged(codes_o, fac_o, Qt, 2.0)
