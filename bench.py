@@ -171,9 +171,10 @@ def workload_desc(w, name, precision, plan, code_bytes):
             "l2": "inputs (%.2f GB) larger than L2 (129 MB): no flush" % (w["n"] * w["d"] * 4 / 1e9)}
 
 
-def cpu_baseline(w, X_dev, target_s=12.0):
+def cpu_baseline(w, X_dev, target_s=12.0, chunk=100000):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of
-    the same workload (fit on its own subsample, not timed)."""
+    the same workload: the rows it encodes in about `target_s` seconds, in
+    chunks of `chunk` rows (model fitted on 50,000 rows, not timed)."""
     import oracle as O
     fit_rows = min(w["n"], 50000)
     Xf = X_dev[:fit_rows].cpu().numpy()
@@ -182,14 +183,19 @@ def cpu_baseline(w, X_dev, target_s=12.0):
     t0 = time.perf_counter()
     O.encode(probe, mo, rounds=w["rounds"])
     per = (time.perf_counter() - t0) / probe.shape[0]
-    ns = int(min(fit_rows, max(2000, target_s / max(per, 1e-9))))
-    Xs = Xf[:ns]
-    t0 = time.perf_counter()
-    enc = O.encode(Xs, mo, rounds=w["rounds"])
-    dt = time.perf_counter() - t0
+    ns = int(min(w["n"], max(2000, target_s / max(per, 1e-9))))
+    dt = 0.0
+    enc = None
+    for r0 in range(0, ns, chunk):
+        Xs = X_dev[r0:min(ns, r0 + chunk)].cpu().numpy()
+        t0 = time.perf_counter()
+        e = O.encode(Xs, mo, rounds=w["rounds"])
+        dt += time.perf_counter() - t0
+        if enc is None:
+            enc = e
     return {"value": ns / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-            "sample": "%d rows of the workload (oracle fit on %d rows, not timed): "
-                      "FP64 projection + CAQ + factors, %.1f s" % (ns, fit_rows, dt)}, mo, enc
+            "sample": "%d rows of the workload in chunks of %d (oracle fit on %d rows, not timed): "
+                      "FP64 projection + CAQ + factors, %.1f s" % (ns, chunk, fit_rows, dt)}, mo, enc
 
 
 # Algorithmic lane operations of quantize / adjust / pack (Eq. find_nearest_code,
@@ -308,9 +314,8 @@ def run_ours(args):
     t_max = max_over_ranks(world, t_dev)
     value = n * world * args.steps / t_max
 
-    # kernel times per step from the timed region (the encode overlaps the
-    # projection of one chunk with the quantization of the previous one, so a
-    # launch's duration includes the sharing of the SMs)
+    # kernel times per step from the timed region (each chunk of rows is
+    # projected, then quantized, on the caller's stream)
     (ms_p, l_p), (ms_q, l_q) = ktimes["projection"], ktimes["quantize_adjust_pack"]
     t_proj = ms_p / 1e3 / args.steps
     t_caq = ms_q / 1e3 / args.steps
@@ -402,6 +407,22 @@ def run_ours(args):
                            "tensor_cores": m.tensor_cores}
         m.set_precision(args.precision)
 
+    # distance estimation on the encoded batch (Sec. 3.2 estimator, b-bit
+    # prefixes, Sec. 4.3 multi-stage bounds): query-vector pairs per second
+    est = None
+    if not args.no_estimator and rank == 0:
+        ne, nqe = min(n, 100000), 100
+        Qe = synth.queries(nqe, d, w["alpha"]).to(dev)
+        ce, fe = codes[:ne], factors[:ne]
+        est = {"n": ne, "nq": nqe}
+        for name, fn in (("estimate", lambda: m.estimate_dist(ce, fe, Qe)),
+                         ("prefix_2bit", lambda: m.estimate_dist(ce, fe, Qe, prefix_bits=2)),
+                         ("staged_m2", lambda: m.estimate_staged(ce, fe, Qe, 2.0))):
+            fn()
+            t = time_events(fn, 3, stream)
+            est[name + "_pairs_per_s"] = ne * nqe / t
+        del Qe
+
     # serving form: Poisson stream of insert requests over three collections
     ingest = None
     if not args.no_ingest and rank == 0:
@@ -440,7 +461,7 @@ def run_ours(args):
                "step_roofline_vectors_per_s": step_roof,
                "step_roofline_frac": value / world / step_roof,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-               "clocks": clocks, "precision_forms": forms, "ingest": ingest}
+               "clocks": clocks, "precision_forms": forms, "estimator": est, "ingest": ingest}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -474,12 +495,18 @@ def serving_run(args, dev):
         fb = torch.empty((nr, m.factor_count), dtype=torch.float32).pin_memory()
         reqs.append((c, Xr, cb, fb))
     svc = P.Ingest(models, hbm_budget_bytes=40 << 30, max_batch_rows=65536, slots=4)
-    # capacity of the service on this request mix: everything submitted at once
-    t0 = time.perf_counter()
-    tk = [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs]
-    for t in tk:
+    # warm-up: a few requests of each collection
+    for t in [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs[:30]]:
         svc.wait(t, timeout_ms=120000)
-    sat_s = time.perf_counter() - t0
+    # capacity of the service on this request mix: everything submitted at
+    # once, the better of two passes
+    sat_s = float("inf")
+    for _ in range(2):
+        t0 = time.perf_counter()
+        tk = [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs]
+        for t in tk:
+            svc.wait(t, timeout_ms=120000)
+        sat_s = min(sat_s, time.perf_counter() - t0)
     capacity = sum(sizes) / sat_s
     # Poisson arrivals at load factor rho of that capacity
     rate = args.ingest_load * capacity / float(np.mean(sizes))  # requests / s
@@ -530,6 +557,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-ingest", action="store_true")
+    ap.add_argument("--no-estimator", action="store_true")
     ap.add_argument("--ingest-vectors", type=int, default=2_000_000)
     ap.add_argument("--ingest-load", type=float, default=0.8)
     args = ap.parse_args()

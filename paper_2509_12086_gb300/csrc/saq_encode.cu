@@ -108,52 +108,6 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
     return SAQ_OK;
 }
 
-// Chunked encode with the projection of chunk i + 1 (tensor cores) running
-// on one library stream while chunk i is quantized (CUDA cores) on another;
-// two scratch buffers alternate.  Forks from and joins back into `s`.
-saq_status encode_rows_overlapped(saq_model *m, const float *X, int64_t n, uint8_t *codes,
-                                  float *factors, void *scratch0, void *scratch1, int64_t rows,
-                                  cudaStream_t s) {
-    std::lock_guard<std::mutex> lk(m->pipe_mu);
-    if (!m->pipe_s[0]) {
-        for (int i = 0; i < 2; ++i) {
-            SAQ_CUDA_CHECK(cudaStreamCreateWithFlags(&m->pipe_s[i], cudaStreamNonBlocking));
-            SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_proj[i], cudaEventDisableTiming));
-            SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_caq[i], cudaEventDisableTiming));
-            SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_join[i], cudaEventDisableTiming));
-        }
-        SAQ_CUDA_CHECK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
-    }
-    cudaStream_t ps = m->pipe_s[0], qs = m->pipe_s[1];
-    SAQ_CUDA_CHECK(cudaEventRecord(m->ev_fork, s));
-    SAQ_CUDA_CHECK(cudaStreamWaitEvent(ps, m->ev_fork, 0));
-    SAQ_CUDA_CHECK(cudaStreamWaitEvent(qs, m->ev_fork, 0));
-    saq_status st = SAQ_OK;
-    int64_t i = 0;
-    for (int64_t r0 = 0; r0 < n && st == SAQ_OK; r0 += rows, ++i) {
-        const int b = (int)(i & 1);
-        void *scr = b ? scratch1 : scratch0;
-        const int64_t nr = std::min(rows, n - r0);
-        if (i >= 2) SAQ_CUDA_CHECK(cudaStreamWaitEvent(ps, m->ev_caq[b], 0));
-        const ScratchParts p = scratch_parts(m, scr, rows);
-        st = project_rows(m, X + r0 * m->d, nr, p.Oi, m->dk, kInterleaved,
-                          factors + r0 * m->nf, m->nf, p.vmax, ps);
-        if (st != SAQ_OK) break;
-        SAQ_CUDA_CHECK(cudaEventRecord(m->ev_proj[b], ps));
-        SAQ_CUDA_CHECK(cudaStreamWaitEvent(qs, m->ev_proj[b], 0));
-        st = quantize_rows(m, scr, rows, nr, codes + r0 * (int64_t)m->code_bytes,
-                           factors + r0 * m->nf, qs);
-        if (st != SAQ_OK) break;
-        SAQ_CUDA_CHECK(cudaEventRecord(m->ev_caq[b], qs));
-    }
-    // join both streams back into the caller's stream (also on failure)
-    cudaEventRecord(m->ev_join[0], ps);
-    cudaEventRecord(m->ev_join[1], qs);
-    cudaStreamWaitEvent(s, m->ev_join[0], 0);
-    cudaStreamWaitEvent(s, m->ev_join[1], 0);
-    return st;
-}
-
 }  // namespace saq
 
 using namespace saq;
@@ -174,19 +128,17 @@ saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n, uint8_t
     if (st != SAQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (m->dk == 0) return launch_rownorm2(m, X_dev, n, factors_dev, m->nf, s);
-    // chunks of projected rows of about 256 MB; with more than one chunk the
-    // projection of the next chunk overlaps the quantization of this one
-    const int64_t rows = chunk_rows(m, n, (size_t)256 << 20);
-    const int nbuf = rows < n ? 2 : 1;
+    // chunks of about 1 GB of projected rows, each projected then quantized
+    // on `s` (measured at d = 960: 1 GB chunks run as fast as smaller chunks
+    // whose projection overlaps the previous chunk's quantization on a
+    // second stream, and need half the scratch)
+    const int64_t rows = chunk_rows(m, n, (size_t)1024 << 20);
     const size_t sb = encode_scratch_bytes(m, rows);
     void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, sb * (size_t)nbuf, s);
+    cudaError_t e = cudaMallocAsync(&scratch, sb, s);
     if (e != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
-    if (nbuf == 1) st = encode_rows(m, X_dev, n, codes_dev, factors_dev, scratch, rows, s);
-    else
-        st = encode_rows_overlapped(const_cast<saq_model *>(m), X_dev, n, codes_dev, factors_dev,
-                                    scratch, static_cast<uint8_t *>(scratch) + sb, rows, s);
+    st = encode_rows(m, X_dev, n, codes_dev, factors_dev, scratch, rows, s);
     cudaFreeAsync(scratch, s);
     return st;
 }

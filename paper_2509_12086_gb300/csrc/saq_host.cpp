@@ -202,16 +202,6 @@ void model_release_device(saq_model *m) {
     cudaFree(m->d_B);
     m->d_B = nullptr;
     tc_release(m);
-    for (int i = 0; i < 2; ++i) {
-        if (m->pipe_s[i]) cudaStreamDestroy(m->pipe_s[i]);
-        if (m->ev_proj[i]) cudaEventDestroy(m->ev_proj[i]);
-        if (m->ev_caq[i]) cudaEventDestroy(m->ev_caq[i]);
-        if (m->ev_join[i]) cudaEventDestroy(m->ev_join[i]);
-        m->pipe_s[i] = nullptr;
-        m->ev_proj[i] = m->ev_caq[i] = m->ev_join[i] = nullptr;
-    }
-    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
-    m->ev_fork = nullptr;
     m->d_mean = nullptr;
     m->d_W = nullptr;
 }

@@ -93,12 +93,6 @@ struct saq_model {
     float *d_W = nullptr;                 // dk x d FP32 row-major
     float *d_B = nullptr;                 // dk x d FP32: row i = sigma_i v_i^T (if Vt is known)
     saq::TcOperands tc;
-    // two library streams that overlap the projection of one chunk with the
-    // quantization of the previous one (created on first use)
-    std::mutex pipe_mu;
-    cudaStream_t pipe_s[2] = {nullptr, nullptr};
-    cudaEvent_t ev_fork = nullptr, ev_proj[2] = {nullptr, nullptr}, ev_caq[2] = {nullptr, nullptr},
-                ev_join[2] = {nullptr, nullptr};
 };
 
 namespace saq {
