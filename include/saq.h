@@ -146,8 +146,9 @@ saq_status saq_model_set_rounds(saq_model *m, int32_t rounds);
  * ends the segment early, which changes no result); then the factors and the
  * bit-plane codes.  Outputs: codes_dev n x code_bytes, factors_dev
  * n x factor_count FP32.  Asynchronous on `stream`.  n == 0 is a no-op.
- * Scratch memory comes from the stream-ordered allocator (cudaMallocAsync)
- * and is returned before the call's work completes on the stream.
+ * Scratch memory comes from a stream-ordered pool the library keeps per
+ * device (memory up to 8 GB stays cached between calls) and is returned
+ * before the call's work completes on the stream.
  */
 saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n,
                       uint8_t *codes_dev, float *factors_dev, void *stream);

@@ -135,7 +135,7 @@ saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n, uint8_t
     const int64_t rows = chunk_rows(m, n, (size_t)1024 << 20);
     const size_t sb = encode_scratch_bytes(m, rows);
     void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, sb, s);
+    cudaError_t e = scratch_alloc(&scratch, sb, s);
     if (e != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
     st = encode_rows(m, X_dev, n, codes_dev, factors_dev, scratch, rows, s);
@@ -195,7 +195,7 @@ saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
     st = launch_copy_strided(norms2_dev, 1, factors_dev, m->nf, n, s);
     if (st != SAQ_OK || m->dk == 0) return st;
     void *scratch = nullptr;
-    if (cudaMallocAsync(&scratch, encode_scratch_bytes(m, n), s) != cudaSuccess)
+    if (scratch_alloc(&scratch, encode_scratch_bytes(m, n), s) != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed");
     const ScratchParts p = scratch_parts(m, scratch, n);
     st = launch_seg_vmax(m, O_dev, n, p.vmax, s);
@@ -221,7 +221,7 @@ saq_status saq_quantize_projected(const saq_model *m, const float *O_dev,
     st = launch_copy_strided(norms2_dev, 1, factors_dev, m->nf, n, s);
     if (st != SAQ_OK || m->dk == 0) return st;
     void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, encode_scratch_bytes(m, n), s);
+    cudaError_t e = scratch_alloc(&scratch, encode_scratch_bytes(m, n), s);
     if (e != cudaSuccess)
         return set_error(SAQ_ERR_OOM, "scratch allocation failed: %s", cudaGetErrorString(e));
     const ScratchParts p = scratch_parts(m, scratch, n);
@@ -243,73 +243,89 @@ saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
     saq_status st = check_device(m);
     if (st != SAQ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // Two pipeline slots: the copy-in of chunk i+1 and the copy-out of chunk
-    // i-1 overlap the encode of chunk i (copy and compute on separate
-    // streams, ordered by events).
-    const int64_t rows = std::min<int64_t>(n, 65536);
-    const size_t xb = sizeof(float) * (size_t)rows * m->d;
-    const size_t cb = m->code_bytes * (size_t)rows;
-    const size_t fb = sizeof(float) * (size_t)rows * m->nf;
-    const size_t ob = encode_scratch_bytes(m, rows);
-    uint8_t *buf[2] = {nullptr, nullptr};
-    void *O = nullptr;
-    cudaStream_t cs[2] = {nullptr, nullptr};
-    cudaEvent_t in_done[2] = {nullptr, nullptr}, enc_done[2] = {nullptr, nullptr},
-                out_done[2] = {nullptr, nullptr};
+    // kSlots staging slots of about 512 MB of rows; a copy-in stream and a
+    // copy-out stream (the two copy engines) run beside the encode on `s`:
+    // the copy-in of chunk i+1 and the copy-out of chunk i-1 overlap the
+    // encode of chunk i.  Buffers come from the stream-ordered pool.
+    constexpr int kSlots = 3;
+    const int64_t rows = std::min<int64_t>(
+        n, std::max<int64_t>(32, ((int64_t)(512 << 20) / (4 * (int64_t)m->d)) / 32 * 32));
     auto round16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-    const size_t slot = round16(xb) + round16(cb) + round16(fb);
+    const size_t xb = round16(sizeof(float) * (size_t)rows * m->d);
+    const size_t cb = round16(m->code_bytes * (size_t)rows);
+    const size_t fb = round16(sizeof(float) * (size_t)rows * m->nf);
+    const size_t slot = xb + cb + fb;
+    const size_t ob = m->dk > 0 ? encode_scratch_bytes(m, rows) : 0;
+    uint8_t *buf = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ready = nullptr, done_in = nullptr, done_out = nullptr;
+    cudaEvent_t in_done[kSlots] = {}, enc_done[kSlots] = {}, out_done[kSlots] = {};
     auto cleanup = [&]() {
-        for (int i = 0; i < 2; ++i) {
-            if (cs[i]) cudaStreamSynchronize(cs[i]);
+        // join the copy streams into `s`, then return the buffers
+        if (d2h && done_out) {
+            cudaEventRecord(done_out, d2h);
+            cudaStreamWaitEvent(s, done_out, 0);
         }
+        if (h2d && done_in) {
+            cudaEventRecord(done_in, h2d);
+            cudaStreamWaitEvent(s, done_in, 0);
+        }
+        if (buf) cudaFreeAsync(buf, s);
         cudaStreamSynchronize(s);
-        for (int i = 0; i < 2; ++i) {
-            cudaFree(buf[i]);
-            if (cs[i]) cudaStreamDestroy(cs[i]);
-            if (in_done[i]) cudaEventDestroy(in_done[i]);
-            if (enc_done[i]) cudaEventDestroy(enc_done[i]);
-            if (out_done[i]) cudaEventDestroy(out_done[i]);
-        }
-        cudaFree(O);
+        if (h2d) cudaStreamDestroy(h2d);
+        if (d2h) cudaStreamDestroy(d2h);
+        for (cudaEvent_t e : {ready, done_in, done_out}) if (e) cudaEventDestroy(e);
+        for (int i = 0; i < kSlots; ++i)
+            for (cudaEvent_t e : {in_done[i], enc_done[i], out_done[i]}) if (e) cudaEventDestroy(e);
     };
-    for (int i = 0; i < 2; ++i) {
-        if (cudaMalloc(&buf[i], slot) != cudaSuccess) { cleanup(); return set_error(SAQ_ERR_OOM, "staging allocation failed"); }
-        if (cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&in_done[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&enc_done[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&out_done[i], cudaEventDisableTiming) != cudaSuccess) {
-            cleanup();
-            return set_error(SAQ_ERR_CUDA, "stream/event creation failed");
-        }
+    bool ok = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t *e : {&ready, &done_in, &done_out})
+        ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < kSlots && ok; ++i)
+        for (cudaEvent_t *e : {&in_done[i], &enc_done[i], &out_done[i]})
+            ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cleanup();
+        return set_error(SAQ_ERR_CUDA, "stream/event creation failed");
     }
-    if (cudaMalloc(&O, ob) != cudaSuccess) { cleanup(); return set_error(SAQ_ERR_OOM, "scratch allocation failed"); }
-    st = SAQ_OK;
+    if (scratch_alloc((void **)&buf, slot * kSlots + ob, s) != cudaSuccess) {
+        buf = nullptr;
+        cleanup();
+        return set_error(SAQ_ERR_OOM, "staging allocation failed");
+    }
+    void *O = buf + slot * kSlots;
+    // the copy streams may use the buffers once the allocation is ordered
+    cudaEventRecord(ready, s);
+    cudaStreamWaitEvent(h2d, ready, 0);
+    cudaStreamWaitEvent(d2h, ready, 0);
     int64_t chunk = 0;
     for (int64_t r0 = 0; r0 < n && st == SAQ_OK; r0 += rows, ++chunk) {
-        const int sl = (int)(chunk & 1);
+        const int sl = (int)(chunk % kSlots);
         const int64_t nr = std::min(rows, n - r0);
-        float *dx = (float *)buf[sl];
-        uint8_t *dc = buf[sl] + round16(xb);
-        float *df = (float *)(buf[sl] + round16(xb) + round16(cb));
-        // the slot's previous copy-out must be done before it is overwritten
-        cudaStreamWaitEvent(cs[sl], out_done[sl], 0);
+        uint8_t *base = buf + slot * (size_t)sl;
+        float *dx = (float *)base;
+        uint8_t *dc = base + xb;
+        float *df = (float *)(base + xb + cb);
+        // the slot's previous copy-out must be done before it is refilled
+        if (chunk >= kSlots) cudaStreamWaitEvent(h2d, out_done[sl], 0);
         cudaMemcpyAsync(dx, X_host + r0 * m->d, sizeof(float) * (size_t)nr * m->d,
-                        cudaMemcpyHostToDevice, cs[sl]);
-        cudaEventRecord(in_done[sl], cs[sl]);
+                        cudaMemcpyHostToDevice, h2d);
+        cudaEventRecord(in_done[sl], h2d);
         cudaStreamWaitEvent(s, in_done[sl], 0);
         if (m->dk == 0) st = launch_rownorm2(m, dx, nr, df, m->nf, s);
         else st = encode_rows(m, dx, nr, dc, df, O, rows, s);
         cudaEventRecord(enc_done[sl], s);
-        cudaStreamWaitEvent(cs[sl], enc_done[sl], 0);
+        cudaStreamWaitEvent(d2h, enc_done[sl], 0);
         if (m->code_bytes)
             cudaMemcpyAsync(codes_host + r0 * (int64_t)m->code_bytes, dc, m->code_bytes * (size_t)nr,
-                            cudaMemcpyDeviceToHost, cs[sl]);
+                            cudaMemcpyDeviceToHost, d2h);
         cudaMemcpyAsync(factors_host + r0 * m->nf, df, sizeof(float) * (size_t)nr * m->nf,
-                        cudaMemcpyDeviceToHost, cs[sl]);
-        cudaEventRecord(out_done[sl], cs[sl]);
+                        cudaMemcpyDeviceToHost, d2h);
+        cudaEventRecord(out_done[sl], d2h);
     }
-    cudaError_t e = cudaGetLastError();
     cleanup();
+    cudaError_t e = cudaGetLastError();
     if (st != SAQ_OK) return st;
     if (e != cudaSuccess) return set_error(SAQ_ERR_CUDA, "encode_host: %s", cudaGetErrorString(e));
     return SAQ_OK;
@@ -344,9 +360,9 @@ saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
     float *qrot = nullptr, *qn2 = nullptr, *vs = nullptr;
     const size_t bq = sizeof(float) * (size_t)nq * std::max(1, m->dk);
     const size_t bv = sizeof(float) * (size_t)n * std::max<size_t>(1, nk);
-    if (cudaMallocAsync((void **)&qrot, bq, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&qn2, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&vs, bv, s) != cudaSuccess) {
+    if (scratch_alloc((void **)&qrot, bq, s) != cudaSuccess ||
+        scratch_alloc((void **)&qn2, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
+        scratch_alloc((void **)&vs, bv, s) != cudaSuccess) {
         if (qrot) cudaFreeAsync(qrot, s);
         if (qn2) cudaFreeAsync(qn2, s);
         return set_error(SAQ_ERR_OOM, "scratch allocation failed");
@@ -386,10 +402,10 @@ saq_status saq_estimate_staged(const saq_model *m, const uint8_t *codes_dev,
     const size_t nk = std::max<size_t>(1, m->kept.size());
     float *qrot = nullptr, *qn2 = nullptr, *vs = nullptr, *qsig = nullptr;
     const size_t bq = sizeof(float) * (size_t)nq * std::max(1, m->dk);
-    if (cudaMallocAsync((void **)&qrot, bq, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&qn2, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&vs, sizeof(float) * (size_t)n * nk, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&qsig, sizeof(float) * (size_t)nq * nk, s) != cudaSuccess) {
+    if (scratch_alloc((void **)&qrot, bq, s) != cudaSuccess ||
+        scratch_alloc((void **)&qn2, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
+        scratch_alloc((void **)&vs, sizeof(float) * (size_t)n * nk, s) != cudaSuccess ||
+        scratch_alloc((void **)&qsig, sizeof(float) * (size_t)nq * nk, s) != cudaSuccess) {
         if (qrot) cudaFreeAsync(qrot, s);
         if (qn2) cudaFreeAsync(qn2, s);
         if (vs) cudaFreeAsync(vs, s);

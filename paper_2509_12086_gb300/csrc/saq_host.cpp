@@ -35,6 +35,39 @@ static std::atomic<uint64_t> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
 
 namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pool[dev], &props);
+            if (e != cudaSuccess) {
+                g_pool[dev] = nullptr;
+                return e;
+            }
+            // without a threshold the pool unmaps its memory at every
+            // synchronisation, and the next call maps it again
+            uint64_t keep = kPoolKeepBytes;
+            cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+namespace {
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;

@@ -107,6 +107,10 @@ int plan_search(const double *sig2, int D, int g, int64_t quota_bits,
 void philox_gaussian(uint64_t seed, uint64_t stream_id, double *out, size_t n);
 
 saq_status model_finalize(saq_model *m);  // derive kept segs, upload
+// Stream-ordered scratch from the library's own pool on the current device
+// (kept cached up to kPoolKeepBytes between calls); free with cudaFreeAsync.
+constexpr size_t kPoolKeepBytes = (size_t)8 << 30;
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
 saq_status model_upload_basis(saq_model *m);  // d_B from Vt and sig2
 saq_status model_build_tc(saq_model *m, int precision, cudaStream_t s);
 void model_release_device(saq_model *m);
