@@ -41,9 +41,9 @@ UNIT = "vectors/s"
 # traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "8833e5c93d3f8552397c2db070d9ff890bb26e80",
+    "projection": {"src": "k_tc.cu", "sha1": "a039bb6907b57e43e708777eb3e3506e1d84fab0",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258.173952e6 + 212.143360e6) / 65536},
+                   "bytes_per_row": (258.195200e6 + 211.114752e6) / 65536},
     "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "336b7ac207606ab9096ff4ad2b96f712923b8f1b",
                              "workload": "c2_d960", "precision": "fp32",
                              "bytes_per_row": (1981.201e6 + 275.075840e6) / 65536},

@@ -12,13 +12,14 @@
 //               64-byte rows of a tensor copy;
 //   warp 1      TMEM owner and MMA issuer (one elected lane): tcgen05.mma,
 //               accumulator 128 lanes x NP FP32 columns in TMEM;
-//   warps 2-9   converters, then epilogue.  Two threads per tile row (one per
-//               half of the K block): read the staged X values, centre and
-//               scale them with one FMA against -c*s kept in shared memory,
-//               convert them into the A operand(s) (UMMA K-major, 64-byte
-//               rows, 64-byte swizzle) and accumulate |x - c|^2; after the K
-//               loop each warp drains its TMEM lane quadrant for half of the
-//               columns with tcgen05.ld.
+//   warps 2-9   converters, then epilogue.  Two groups of four warps take
+//               alternate K blocks (two blocks in conversion at once); in a
+//               group one thread per tile row reads the staged X values,
+//               centres and scales them with one FMA against -c*s kept in
+//               shared memory, converts them into the A operand(s) (UMMA
+//               K-major, 64-byte rows, 64-byte swizzle) and accumulates
+//               |x - c|^2; after the K loop each warp drains its TMEM lane
+//               quadrant for alternate 16-column chunks with tcgen05.ld.
 // Operand rows are 64 bytes per stage (32 FP16/BF16 or 64 E4M3 values), so
 // three or more stages fit in shared memory.
 // Precision modes:
@@ -299,7 +300,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&conv[s], kConvWarps);
+            mbar_init(&conv[s], kConvWarps / 2);  // one group of converters per block
             mbar_init(&empty[s], 1);
         }
         mbar_init(accf, 1);
@@ -384,33 +385,43 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
         }
         __syncwarp();
     } else {
-        // ---- converters: two threads per tile row, one per half of a K block
+        // ---- converters: two groups of four warps, group h converting the K
+        // blocks kb = h, h + 2, ... (one thread per tile row, the whole block),
+        // so that two blocks are converted at once
         const int q = warp & 3;
         const int r = q * 32 + lane;
         const int h = (warp - 2) >> 2;
         const bool row_ok = row0 + r < n;
         float nrm = 0.f;
         bool ok = true;
-        for (int kb = 0; kb < nkb && ok; ++kb) {
+        for (int kb = h; kb < nkb && ok; kb += 2) {
             const int s = kb % C::STAGES;
             const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
             int got = 0;
-            if (lane == 0) got = mbar_wait(&full[s], ph, abort_flag, err, 3) ? 1 : 0;
+            // The other group may not have consumed this stage's previous block
+            // yet; a parity wait cannot tell phase p from phase p + 2, so first
+            // wait until the MMAs of block kb - STAGES are done (the stage's
+            // barriers are then one phase behind this block at most).
+            if (lane == 0)
+                got = (kb < C::STAGES || mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 5)) &&
+                              mbar_wait(&full[s], ph, abort_flag, err, 3)
+                          ? 1
+                          : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) { ok = false; break; }
             uint8_t *st = smem + s * SB;
             uint8_t *a0 = st + a_offset<MODE>();
             const float *mk = mcs + kb * C::BK;
             if (MODE == kFP8) {
-                // 2 chunks of 16 E4M3 (32 values) per thread, all from staged box h
+                // 4 chunks of 16 E4M3 (64 values) per thread, from the two staged boxes
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int ac = 2 * h + i;  // operand chunk: values ac*16 .. ac*16+15
-                    const uint8_t *xb = st + h * kXBox;
+                for (int i = 0; i < 4; ++i) {
+                    const int ac = i;  // operand chunk: values ac*16 .. ac*16+15
+                    const uint8_t *xb = st + (i >> 1) * kXBox;
                     uint32_t w[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int c = i * 4 + e;  // staged chunk within box h
+                        const int c = (i & 1) * 4 + e;  // staged chunk within its box
                         const float4 x = *reinterpret_cast<const float4 *>(xb + swz128(r, c));
                         const float4 m = *reinterpret_cast<const float4 *>(mk + ac * 16 + e * 4);
                         const float y0 = fmaf(x.x, x_scale, m.x), y1 = fmaf(x.y, x_scale, m.y);
@@ -427,10 +438,10 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                 }
             } else {
                 uint8_t *a1 = a0 + kATile;
-                // 2 chunks of 8 values (16 values) per thread from the staged box
+                // 4 chunks of 8 values (32 values) per thread from the staged box
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int ac = 2 * h + i;  // operand chunk: values ac*8 .. ac*8+7
+                for (int i = 0; i < 4; ++i) {
+                    const int ac = i;  // operand chunk: values ac*8 .. ac*8+7
                     const float4 x0 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac));
                     const float4 x1 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac + 1));
                     const float4 m0 = *reinterpret_cast<const float4 *>(mk + ac * 8);
@@ -467,7 +478,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv[s]);
         }
-        // |x - c|^2 of the row: the two halves meet in shared memory
+        // |x - c|^2 of the row: the two groups' partial sums meet in shared memory
         if (h == 1) nrm_half[r] = nrm;
         named_sync(1, 32 * kConvWarps);
         if (h == 0 && pass == 0 && row_ok && norms && ok)
