@@ -55,8 +55,13 @@ __device__ __forceinline__ int pack_segment(const uint8_t *cp, int len, bool val
     int S = 0;
     for (int j0 = 0; j0 < len; j0 += kU) {
         int c[kU];
+        if (j0 + kU <= len) {
 #pragma unroll
-        for (int k = 0; k < kU; ++k) c[k] = j0 + k < len ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
+            for (int k = 0; k < kU; ++k) c[k] = (int)cp[(int64_t)(j0 + k) << 5];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kU; ++k) c[k] = j0 + k < len ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
+        }
         // plane p of the kU codes as the bits of one byte (past the end: 0)
 #pragma unroll
         for (int p = 0; p < B; ++p) {
@@ -68,7 +73,7 @@ __device__ __forceinline__ int pack_segment(const uint8_t *cp, int len, bool val
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
             const int u = 2 * c[k] - cmax;
-            S += j0 + k < len ? u * u : 0;
+            S += j0 + k < len ? u * u : 0;  // a code past the end reads 0, not a code
         }
         if (((j0 + kU) & 63) == 0 || j0 + kU >= len) {
             if (valid) {
@@ -108,33 +113,34 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
     const bool live = valid && vmax > 0.f;
     // initial codes, Eq. find_nearest_code: c = floor((o + v_max) / Delta),
     // Delta = 2 v_max / 2^B; with I = <u, o>, S = |u|^2 and |o|^2
+    // (in FP32: the code c as a float, clamped, its byte from the bits of
+    // c + 2^23; |u|^2 is summed in FP32 for the decisions and recounted
+    // exactly while packing).  Every lane of the last group of 32 rows reads
+    // rows the buffer holds; a lane past n keeps codes 0.
     const float inv_delta = live ? (float)(1 << (B - 1)) / vmax : 0.f;
-    float I = 0.f, n2 = 0.f;
-    int Si = 0;
-    for (int j0 = 0; j0 < len; j0 += kU) {
+    const float off_c = vmax * inv_delta;  // (o + v_max) / Delta = o / Delta + off_c
+    const float cmaxf = (float)cmax;
+    float I = 0.f, n2 = 0.f, S = 0.f;
+    auto init = [&](float x, int j) {
+        const float cf = fminf(fmaxf(floorf(fmaf(x, inv_delta, off_c)), 0.f), cmaxf);
+        cp[(int64_t)j << 5] = (uint8_t)__float_as_uint(cf + 8388608.f);
+        const float u = fmaf(2.f, cf, -cmaxf);
+        I = fmaf(u, x, I);
+        n2 = fmaf(x, x, n2);
+        S = fmaf(u, u, S);
+    };
+    const int lenU = len & ~(kU - 1);  // coordinates in whole batches
+    for (int j0 = 0; j0 < lenU; j0 += kU) {
         float x[kU];
 #pragma unroll
-        for (int k = 0; k < kU; ++k)
-            x[k] = valid && j0 + k < len ? __ldg(op + ((int64_t)(j0 + k) << 5)) : 0.f;
+        for (int k = 0; k < kU; ++k) x[k] = __ldg(op + ((int64_t)(j0 + k) << 5));
 #pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            if (j0 + k >= len) break;
-            int c = 0;
-            if (live) {
-                c = (int)floorf((x[k] + vmax) * inv_delta);
-                c = c < 0 ? 0 : (c > cmax ? cmax : c);
-            }
-            cp[(int64_t)(j0 + k) << 5] = (uint8_t)c;
-            const int u = 2 * c - cmax;
-            I = fmaf((float)u, x[k], I);
-            n2 = fmaf(x[k], x[k], n2);
-            Si += u * u;
-        }
+        for (int k = 0; k < kU; ++k) init(live ? x[k] : 0.f, j0 + k);
     }
+    for (int j = lenU; j < len; ++j) init(live ? __ldg(op + ((int64_t)j << 5)) : 0.f, j);
     // A lane that is done (no move in its last round, or nothing to adjust)
     // keeps I2 = +inf, which no gain exceeds.
-    float S = (float)Si, I2 = live ? I * I : __int_as_float(0x7f800000);
-    const float cmaxf = (float)cmax;
+    float I2 = live ? I * I : __int_as_float(0x7f800000);
     // one coordinate of Algorithm 1 for this lane.  u = 2c - cmax as a float
     // without a conversion: the bits 0x4B400000 + (2c - cmax) are the float
     // 1.5 * 2^23 + (2c - cmax) exactly (unit spacing there).  s = sign(T)
@@ -154,7 +160,6 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
             moved = true;
         }
     };
-    const int lenU = len & ~(kU - 1);  // coordinates in whole batches
     for (int r = 0; r < rounds; ++r) {
         if (!__any_sync(0xffffffffu, I2 != __int_as_float(0x7f800000))) break;
         bool moved = false;
@@ -171,11 +176,19 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
         for (int j0 = 0; j0 < lenU; j0 += kU) {
             float xn[kU];
             int cn[kU];
+            if (j0 + 2 * kU <= len) {  // the next batch lies inside the segment
 #pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                const int jn = j0 + kU + k;
-                xn[k] = jn < len ? __ldg(op + ((int64_t)jn << 5)) : 0.f;
-                cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
+                for (int k = 0; k < kU; ++k) {
+                    xn[k] = __ldg(op + ((int64_t)(j0 + kU + k) << 5));
+                    cn[k] = (int)cp[(int64_t)(j0 + kU + k) << 5];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kU; ++k) {
+                    const int jn = j0 + kU + k;
+                    xn[k] = jn < len ? __ldg(op + ((int64_t)jn << 5)) : 0.f;
+                    cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
+                }
             }
 #pragma unroll
             for (int k = 0; k < kU; ++k) step(xb[k], cb[k], j0 + k, moved);
@@ -194,6 +207,7 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
 
     // bit-planes from the codes (most significant first, 64-bit words)
     uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
+    int Si;  // |u|^2 of the final codes, exactly
     switch (B) {  // uniform per warp
         case 1: Si = pack_segment<1>(cp, len, valid, cout, words); break;
         case 2: Si = pack_segment<2>(cp, len, valid, cout, words); break;

@@ -357,3 +357,20 @@ def test_c1_staged_estimator_parity(c1):
     assert not m0.has_basis
     with pytest.raises(P.SaqError):
         m0.estimate_staged(codes_o, fac_o, Qt, 2.0)
+
+
+def test_host_path_several_chunks_equals_device_encode():
+    """saq_encode_host stages about 512 MB of rows per chunk in three slots:
+    at d = 4096 that is 32,768 rows, so 100,000 rows run three full chunks
+    and a partial one and reuse a slot; every output must equal the device
+    encode of the same rows."""
+    torch.cuda.set_device(0)
+    d = 4096
+    X = synth.power_law(100_000, d, 0.6, device="cuda")
+    m = P.saq_fit(X[:20000].contiguous(), avg_bits=2.0)
+    cd, fd = m.encode(X)
+    Xh = X.cpu().pin_memory()
+    ch, fh = m.encode_host(Xh)
+    torch.cuda.synchronize()
+    assert torch.equal(ch, cd.cpu())
+    assert torch.equal(fh, fd.cpu())
