@@ -217,8 +217,9 @@ saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
  * device, with that device current); make that first call before any
  * stream capture.  Every call shares the one array, so calls whose work
  * overlaps on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  The array keeps the last call's contents;
- * nothing in it needs to start at zero.
+ * serialised by the caller.  The array keeps the last call's contents:
+ * each call clears the per-segment maxima (which must start at zero) on its
+ * stream before using them; the rest is written before it is read.
  */
 saq_status saq_encode_noalloc(const saq_model *m, const float *X_dev, int64_t n,
                               uint8_t *codes_dev, float *factors_dev, void *stream);
