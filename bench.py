@@ -44,9 +44,9 @@ NCU_TRAFFIC = {
     "projection": {"src": "k_tc.cu", "sha1": "a039bb6907b57e43e708777eb3e3506e1d84fab0",
                    "workload": "c2_d960", "precision": "fp32",
                    "bytes_per_row": (258.195200e6 + 211.114752e6) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "336b7ac207606ab9096ff4ad2b96f712923b8f1b",
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "41fa5c5732a4eb57d6a6a8c58a82ee00eee38bf3",
                              "workload": "c2_d960", "precision": "fp32",
-                             "bytes_per_row": (1981.201e6 + 275.075840e6) / 65536},
+                             "bytes_per_row": (1991.185e6 + 275.891712e6) / 65536},
 }
 
 
