@@ -146,19 +146,23 @@ saq_status saq_model_set_rounds(saq_model *m, int32_t rounds);
  * ends the segment early, which changes no result); then the factors and the
  * bit-plane codes.  Outputs: codes_dev n x code_bytes, factors_dev
  * n x factor_count FP32.  Asynchronous on `stream`.  n == 0 is a no-op.
- * Scratch memory comes from a stream-ordered pool the library keeps per
- * device (memory up to 8 GB stays cached between calls) and is returned
- * before the call's work completes on the stream.
+ * Rows are processed in chunks of about 1 GB of projected rows (projection,
+ * then quantization, per chunk).  Scratch memory (5 bytes per row and kept
+ * dimension of a chunk, plus 4 per row and kept segment) comes from a
+ * stream-ordered pool the library keeps per device (memory up to 8 GB stays
+ * cached between calls) and is returned before the call's work completes on
+ * the stream.
  */
 saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n,
                       uint8_t *codes_dev, float *factors_dev, void *stream);
 
 /*
  * Same as saq_encode, with host buffers: the rows are copied to the device
- * in chunks, encoded and the codes and factors copied back, with copies of
- * one chunk overlapping the encode of the next.  Page-locked host memory is
- * strongly recommended.  Synchronous: returns when the outputs are in host
- * memory.
+ * in chunks of about 512 MB, encoded and the codes and factors copied back,
+ * through three staging slots, with the copy-in of the next chunk and the
+ * copy-out of the previous one (on two streams of their own) overlapping the
+ * encode of the current one.  Page-locked host memory is strongly
+ * recommended.  Synchronous: returns when the outputs are in host memory.
  */
 saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
                            uint8_t *codes_host, float *factors_host,
