@@ -374,3 +374,33 @@ def test_host_path_several_chunks_equals_device_encode():
     torch.cuda.synchronize()
     assert torch.equal(ch, cd.cpu())
     assert torch.equal(fh, fd.cpu())
+
+
+@pytest.mark.parametrize("d,tc", [(6144, True), (6400, False)])
+def test_largest_dimensions(d, tc):
+    """d = 6144 is the largest dimension the tensor-core projection takes
+    (the centring term of a whole row sits in shared memory beside the
+    stages); beyond it an FP32 model projects on the CUDA cores.  Both
+    encodes agree with the oracle."""
+    plan = [(0, 1024, 4), (1024, 2048, 2), (3072, d - 3072, 1)]
+    mo = _random_model(d, plan, seed=d)
+    rng = np.random.default_rng(d)
+    X = (rng.standard_normal((300, d)) * np.linspace(1, 0.05, d)).astype(np.float32)
+    m = lib_model(mo, "fp32")
+    assert m.tensor_cores == tc
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    m.check_device()
+    eo = O.encode(X, mo, rounds=6)
+    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy())
+
+
+def test_more_kept_segments_than_supported_is_an_error():
+    """The quantize kernel takes at most 64 kept segments per model; a plan
+    with more is refused with an error, not encoded."""
+    d = 65 * 16
+    plan = [(i * 16, 16, 2) for i in range(65)]
+    mo = _random_model(d, plan, seed=3)
+    m = lib_model(mo, "fp32")
+    X = torch.randn(64, d, device="cuda")
+    with pytest.raises(P.SaqError):
+        m.encode(X)
