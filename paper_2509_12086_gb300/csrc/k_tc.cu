@@ -214,39 +214,32 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
             smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 consecutive accumulator columns of the warp's lane quadrant (one wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&v)[32]) {
+    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-// both accumulators of the split mode, one wait (one asm statement, so no
-// register is read before the loads have landed)
-__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&v)[16],
-                                            float (&w)[16]) {
-    uint32_t r[16], q[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%32];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
-        "%28,%29,%30,%31}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]),
-          "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]),
-          "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+// the same 32 columns of both accumulators of the split mode, one wait
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float (&v)[32],
+                                            float (&w)[32]) {
+    uint32_t r[32], q[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15]), "=r"(q[16]), "=r"(q[17]), "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]), "=r"(q[23]), "=r"(q[24]), "=r"(q[25]), "=r"(q[26]), "=r"(q[27]), "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
         : "r"(ta), "r"(tb)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {
         v[i] = __uint_as_float(r[i]);
         w[i] = __uint_as_float(q[i]);
     }
@@ -499,37 +492,41 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
             const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
             int si = 0;
             float mx = 0.f;
-            // 16-column chunks, alternating between the two threads of a row
+            // 32-column blocks, alternating between the two threads of a row; a
+            // block past np reads accumulator columns the allocation holds
+            // (np <= 256) and scales from the padded scale vector
 #pragma unroll 1
-            for (int ch = h; ch < (np >> 4); ch += 2) {
-                const int c = ch << 4;
-                float v[16];
+            for (int b = h; b < ((np + 31) >> 5); b += 2) {
+                const int c = b << 5;
+                const int cb = col0 + c;  // first output column of the block
+                float4 sc[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) sc[i] = __ldg(reinterpret_cast<const float4 *>(col_scale + cb) + i);
+                float v[32];
                 if (C::NA == 2) {
-                    float v2[16];
-                    tmem_ld16x2(tq + (uint32_t)c, tq + (uint32_t)(kAcc2 + c), v, v2);
+                    float v2[32];
+                    tmem_ld32x2(tq + (uint32_t)c, tq + (uint32_t)(kAcc2 + c), v, v2);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] += v2[i];
+                    for (int i = 0; i < 32; ++i) v[i] += v2[i];
                 } else {
-                    tmem_ld16(tq + (uint32_t)c, v);
+                    tmem_ld32(tq + (uint32_t)c, v);
                 }
-                const int cb = col0 + c;  // first output column of the chunk
                 if (!row_ok || cb >= dk) continue;
-                const int cn = min(16, dk - cb);
-                const float4 *sc4 = reinterpret_cast<const float4 *>(col_scale + cb);
+                const int cn = min(min(32, np - c), dk - cb);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float4 sc = __ldg(sc4 + i);
-                    v[4 * i] *= sc.x; v[4 * i + 1] *= sc.y; v[4 * i + 2] *= sc.z; v[4 * i + 3] *= sc.w;
+                for (int i = 0; i < 8; ++i) {
+                    v[4 * i] *= sc[i].x; v[4 * i + 1] *= sc[i].y;
+                    v[4 * i + 2] *= sc[i].z; v[4 * i + 3] *= sc[i].w;
                 }
-                if (cn == 16) {
+                if (cn == 32) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
+                    for (int i = 0; i < 32; ++i) {
                         if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
                         else orow[cb + i] = v[i];
                     }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
+                    for (int i = 0; i < 32; ++i) {
                         if (i >= cn) break;
                         if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
                         else orow[cb + i] = v[i];
@@ -541,12 +538,12 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                         mx = 0.f;
                         ++si;
                     }
-                    if (cb + cn <= segc.end[si]) {  // the chunk lies in one segment
+                    if (cb + cn <= segc.end[si]) {  // the block lies in one segment
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) mx = fmaxf(mx, i < cn ? fabsf(v[i]) : 0.f);
+                        for (int i = 0; i < 32; ++i) mx = fmaxf(mx, i < cn ? fabsf(v[i]) : 0.f);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
+                        for (int i = 0; i < 32; ++i) {
                             if (i >= cn) break;
                             while (cb + i >= segc.end[si]) {
                                 if (mx > 0.f)
@@ -771,6 +768,7 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
         return set_error(SAQ_ERR_INVALID, "precision %d has no tensor-core form", precision);
     }
     ex->x_scale = (float)xs;
+    cs.resize(cs.size() + 256, 0.f);  // the epilogue reads whole 32-column blocks
     SAQ_CUDA_CHECK(cudaMalloc(&m->tc.col_scale, sizeof(float) * cs.size()));
     SAQ_CUDA_CHECK(cudaMemcpy(m->tc.col_scale, cs.data(), sizeof(float) * cs.size(),
                               cudaMemcpyHostToDevice));
