@@ -87,9 +87,125 @@ __device__ __forceinline__ int pack_segment(const uint8_t *cp, int len, bool val
     return S;
 }
 
+// The adjustment state of one lane's vector-segment.  A lane that is done
+// (no move in its last round, or nothing to adjust) holds I2 = +inf, which
+// no gain exceeds.
+struct LaneState {
+    float I, S, I2;
+};
+
+// One round of Algorithm 1 over the lane's segment: coordinates j0 + U ..
+// j0 + 2U - 1 are loaded before j0 .. j0 + U - 1 are processed (a code is only
+// written at its own step, so the prefetched codes are current).  u = 2c -
+// cmax is formed as a float without a conversion: the bits 0x4B400000 +
+// (2c - cmax) are the float 1.5 * 2^23 + (2c - cmax) exactly (unit spacing
+// there); s = sign(T) (+ for T = +0); s*u < cmax is the range check of c + s.
+// With PACK_B = B > 0 the round is the last one: a coordinate's code is final
+// once its own step is done, so the bit-planes (most significant first,
+// 64-bit words) and the exact |u|^2, which the function returns, are built
+// as the round goes.
+template <int PACK_B>
+__device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t *cp, int len,
+                                         int cmax, bool &moved, bool valid, uint64_t *cout,
+                                         int words) {
+    const int ubias = 0x4B400000 - cmax;
+    const float cmaxf = (float)cmax;
+    const int lenU = len & ~(kU - 1);  // coordinates in whole batches
+    constexpr int NW = PACK_B > 0 ? PACK_B : 1;
+    uint64_t w[NW];
+#pragma unroll
+    for (int p = 0; p < NW; ++p) w[p] = 0ull;
+    int Si = 0;
+    auto step = [&](float x, int c, int j) {
+        const float u = __int_as_float(ubias + 2 * c) - 12582912.f;
+        const float xS = x * L.S;
+        const float T = fmaf(-u, L.I, xS);
+        const uint32_t sgn = __float_as_uint(T) & 0x80000000u;
+        const float su = __uint_as_float(__float_as_uint(u) ^ sgn);
+        if (su < cmaxf && fmaf(fabsf(T), L.I, x * xS) > L.I2) {
+            L.I = fmaf(__uint_as_float(0x40000000u | sgn), x, L.I);
+            L.S = fmaf(4.f, su, L.S + 4.f);
+            L.I2 = L.I * L.I;
+            c = sgn ? c - 1 : c + 1;
+            cp[(int64_t)j << 5] = (uint8_t)c;
+            moved = true;
+        }
+        return c;
+    };
+    // the final codes cf[0 .. count) of the batch at j0 into the planes
+    auto pack = [&](const int (&cf)[kU], int j0, int count) {
+        if (PACK_B == 0) return;
+#pragma unroll
+        for (int p = 0; p < NW; ++p) {
+            uint32_t b = 0;
+#pragma unroll
+            for (int k = 0; k < kU; ++k)
+                if (k < count) b |= (uint32_t)((cf[k] >> (NW - 1 - p)) & 1) << k;
+            w[p] |= (uint64_t)b << (j0 & 63);
+        }
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            const int u = 2 * cf[k] - cmax;
+            if (k < count) Si += u * u;
+        }
+        if (((j0 + kU) & 63) == 0 || j0 + count >= len) {
+            if (valid) {
+#pragma unroll
+                for (int p = 0; p < NW; ++p) cout[p * words + (j0 >> 6)] = w[p];
+            }
+#pragma unroll
+            for (int p = 0; p < NW; ++p) w[p] = 0ull;
+        }
+    };
+    float xb[kU];
+    int cb[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
+        cb[k] = k < len ? (int)cp[(int64_t)k << 5] : 0;
+    }
+    for (int j0 = 0; j0 < lenU; j0 += kU) {
+        float xn[kU];
+        int cn[kU];
+        if (j0 + 2 * kU <= len) {  // the next batch lies inside the segment
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                xn[k] = __ldg(op + ((int64_t)(j0 + kU + k) << 5));
+                cn[k] = (int)cp[(int64_t)(j0 + kU + k) << 5];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kU; ++k) {
+                const int jn = j0 + kU + k;
+                xn[k] = jn < len ? __ldg(op + ((int64_t)jn << 5)) : 0.f;
+                cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
+            }
+        }
+        int cf[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) cf[k] = step(xb[k], cb[k], j0 + k);
+        pack(cf, j0, kU);
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            xb[k] = xn[k];
+            cb[k] = cn[k];
+        }
+    }
+    // the last, partial batch
+    if (lenU < len) {
+        int cf[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) cf[k] = lenU + k < len ? step(xb[k], cb[k], lenU + k) : 0;
+        pack(cf, lenU, len - lenU);
+    }
+    return Si;
+}
+
 // One warp per (kept segment, group of 32 rows); all kept segments of a
-// chunk in one launch.
-__global__ void __launch_bounds__(256)
+// chunk in one launch.  Four blocks of 256 threads per SM (64 registers):
+// the packing round spills a little, which costs less than the lower
+// occupancy of an uncapped build.
+__global__ void __launch_bounds__(256, 4)
 k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable t, int rounds,
        uint8_t *__restrict__ cs, const float *__restrict__ vmax_arr,
        uint8_t *__restrict__ codes, int64_t code_stride, float *__restrict__ factors, int nf) {
@@ -138,85 +254,41 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
         for (int k = 0; k < kU; ++k) init(live ? x[k] : 0.f, j0 + k);
     }
     for (int j = lenU; j < len; ++j) init(live ? __ldg(op + ((int64_t)j << 5)) : 0.f, j);
-    // A lane that is done (no move in its last round, or nothing to adjust)
-    // keeps I2 = +inf, which no gain exceeds.
-    float I2 = live ? I * I : __int_as_float(0x7f800000);
-    // one coordinate of Algorithm 1 for this lane.  u = 2c - cmax as a float
-    // without a conversion: the bits 0x4B400000 + (2c - cmax) are the float
-    // 1.5 * 2^23 + (2c - cmax) exactly (unit spacing there).  s = sign(T)
-    // (+ for T = +0); s*u < cmax is the range check of c + s.
-    const int ubias = 0x4B400000 - cmax;
-    auto step = [&](float x, int c, int j, bool &moved) {
-        const float u = __int_as_float(ubias + 2 * c) - 12582912.f;
-        const float xS = x * S;
-        const float T = fmaf(-u, I, xS);
-        const uint32_t sgn = __float_as_uint(T) & 0x80000000u;
-        const float su = __uint_as_float(__float_as_uint(u) ^ sgn);
-        if (su < cmaxf && fmaf(fabsf(T), I, x * xS) > I2) {
-            I = fmaf(__uint_as_float(0x40000000u | sgn), x, I);
-            S = fmaf(4.f, su, S + 4.f);
-            I2 = I * I;
-            cp[(int64_t)j << 5] = (uint8_t)(sgn ? c - 1 : c + 1);
-            moved = true;
-        }
-    };
-    for (int r = 0; r < rounds; ++r) {
-        if (!__any_sync(0xffffffffu, I2 != __int_as_float(0x7f800000))) break;
-        bool moved = false;
-        // software pipeline: coordinates j0 + U .. j0 + 2U - 1 are loaded before
-        // j0 .. j0 + U - 1 are processed (a code is only written at its own step,
-        // so the prefetched codes are current)
-        float xb[kU];
-        int cb[kU];
-#pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
-            cb[k] = k < len ? (int)cp[(int64_t)k << 5] : 0;
-        }
-        for (int j0 = 0; j0 < lenU; j0 += kU) {
-            float xn[kU];
-            int cn[kU];
-            if (j0 + 2 * kU <= len) {  // the next batch lies inside the segment
-#pragma unroll
-                for (int k = 0; k < kU; ++k) {
-                    xn[k] = __ldg(op + ((int64_t)(j0 + kU + k) << 5));
-                    cn[k] = (int)cp[(int64_t)(j0 + kU + k) << 5];
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kU; ++k) {
-                    const int jn = j0 + kU + k;
-                    xn[k] = jn < len ? __ldg(op + ((int64_t)jn << 5)) : 0.f;
-                    cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kU; ++k) step(xb[k], cb[k], j0 + k, moved);
-#pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                xb[k] = xn[k];
-                cb[k] = cn[k];
-            }
-        }
-        // the last, partial batch
-#pragma unroll
-        for (int k = 0; k < kU; ++k)
-            if (lenU + k < len) step(xb[k], cb[k], lenU + k, moved);
-        if (!moved) I2 = __int_as_float(0x7f800000);
-    }
-
-    // bit-planes from the codes (most significant first, 64-bit words)
+    LaneState L{I, S, live ? I * I : __int_as_float(0x7f800000)};
     uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
-    int Si;  // |u|^2 of the final codes, exactly
-    switch (B) {  // uniform per warp
-        case 1: Si = pack_segment<1>(cp, len, valid, cout, words); break;
-        case 2: Si = pack_segment<2>(cp, len, valid, cout, words); break;
-        case 3: Si = pack_segment<3>(cp, len, valid, cout, words); break;
-        case 4: Si = pack_segment<4>(cp, len, valid, cout, words); break;
-        case 5: Si = pack_segment<5>(cp, len, valid, cout, words); break;
-        case 6: Si = pack_segment<6>(cp, len, valid, cout, words); break;
-        case 7: Si = pack_segment<7>(cp, len, valid, cout, words); break;
-        default: Si = pack_segment<8>(cp, len, valid, cout, words); break;
+    int Si = -1;  // |u|^2 of the final codes, exactly, once they are packed
+    for (int r = 0; r < rounds; ++r) {
+        if (!__any_sync(0xffffffffu, L.I2 != __int_as_float(0x7f800000))) break;
+        bool moved = false;
+        if (r == rounds - 1) {  // the last round packs as it goes
+            switch (B) {  // uniform per warp
+                case 1: Si = run_round<1>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 2: Si = run_round<2>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 3: Si = run_round<3>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 4: Si = run_round<4>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 5: Si = run_round<5>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 6: Si = run_round<6>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 7: Si = run_round<7>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                default: Si = run_round<8>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+            }
+            break;
+        }
+        run_round<0>(L, op, cp, len, cmax, moved, valid, cout, words);
+        if (!moved) L.I2 = __int_as_float(0x7f800000);
+    }
+    I = L.I;
+    // every lane done before the last round (or no rounds): pack from the codes
+    if (Si < 0) {
+        switch (B) {  // uniform per warp
+            case 1: Si = pack_segment<1>(cp, len, valid, cout, words); break;
+            case 2: Si = pack_segment<2>(cp, len, valid, cout, words); break;
+            case 3: Si = pack_segment<3>(cp, len, valid, cout, words); break;
+            case 4: Si = pack_segment<4>(cp, len, valid, cout, words); break;
+            case 5: Si = pack_segment<5>(cp, len, valid, cout, words); break;
+            case 6: Si = pack_segment<6>(cp, len, valid, cout, words); break;
+            case 7: Si = pack_segment<7>(cp, len, valid, cout, words); break;
+            default: Si = pack_segment<8>(cp, len, valid, cout, words); break;
+        }
     }
     if (valid) {
         float *fo = factors + v * nf;
