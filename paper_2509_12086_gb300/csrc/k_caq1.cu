@@ -19,10 +19,12 @@
 // the convex-cone fact that at most one of +-Delta raises the cosine; the
 // paper's -Delta trial after an accepted +Delta returns to the old point and
 // is rejected.  The range check of c + s reads s*u < 2^B - 1.  A lane whose
-// round made no move stops (its state no longer changes).  v_max comes from the projection (or a separate pass).  Every
-// pass over the coordinates keeps kU loads in flight.  I and S are tracked in
-// FP32 for the decisions; S is recounted exactly from the final codes while
-// they are packed into bit-planes.
+// round made no move stops (its state no longer changes).  v_max comes from
+// the projection (or a separate pass).  Every pass over the coordinates keeps
+// kU loads in flight.  I and S are tracked in FP32 for the decisions; S is
+// recounted exactly from the final codes while they are packed into
+// bit-planes, during the last round (or, for a warp whose lanes all stop
+// earlier, in a pass of its own).
 #include <algorithm>
 
 #include "saq_internal.h"
