@@ -41,12 +41,12 @@ UNIT = "vectors/s"
 # traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "a039bb6907b57e43e708777eb3e3506e1d84fab0",
+    "projection": {"src": "k_tc.cu", "sha1": "a49c6576d534ffbf05fb7341cbb4541993011b71",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258.195200e6 + 211.114752e6) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "41fa5c5732a4eb57d6a6a8c58a82ee00eee38bf3",
+                   "bytes_per_row": (258.240256e6 + 214.483712e6) / 65536},
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "4684b42f517e362c47bdb9b420470a73dfcf2de7",
                              "workload": "c2_d960", "precision": "fp32",
-                             "bytes_per_row": (1991.185e6 + 275.891712e6) / 65536},
+                             "bytes_per_row": (1979.591e6 + 287.465728e6) / 65536},
 }
 
 
