@@ -98,6 +98,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def ready(self, timeout_s=5.0):
+        """Wait for nvidia-smi's first sample, then drop what came before the
+        timed region."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+        self.lines.clear()
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -301,6 +309,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
+    clk.ready()
     l0 = P.saq_kernel_launch_count()
     P.saq_kernel_timing(True)
     t_dev = time_events(step, args.steps, stream) * args.steps
@@ -544,7 +553,7 @@ def tc_enabled(m):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_d960", choices=list(synth.WORKLOADS))
