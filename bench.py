@@ -44,9 +44,9 @@ NCU_TRAFFIC = {
     "projection": {"src": "k_tc.cu", "sha1": "a49c6576d534ffbf05fb7341cbb4541993011b71",
                    "workload": "c2_d960", "precision": "fp32",
                    "bytes_per_row": (258.240256e6 + 214.483712e6) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "4684b42f517e362c47bdb9b420470a73dfcf2de7",
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ffb094df723d5f82f42d644a9eb4cc3d9a4c3090",
                              "workload": "c2_d960", "precision": "fp32",
-                             "bytes_per_row": (1979.591e6 + 287.465728e6) / 65536},
+                             "bytes_per_row": (1981.363e6 + 287.469824e6) / 65536},
 }
 
 
@@ -217,16 +217,18 @@ ALU_INIT, ALU_TRIAL, ALU_ACCEPT, ALU_PACK = 7, 6, 4, 2
 
 
 def alu_ops_per_vector(enc, mo, rounds):
-    """Lane operations per vector counted from the oracle's accept statistics:
-    a vector-segment runs rounds through its first round without an accept."""
-    ops = 0.0
+    """Lane operations and round lane-steps (coordinate trials) per vector,
+    counted from the oracle's accept statistics: a vector-segment runs rounds
+    through its first round without an accept."""
+    ops, steps = 0.0, 0.0
     for j, (off, l, b) in enumerate(mo.kept):
         a = enc.accepts[:, j, :rounds]
         zero = a == 0
         ran = np.where(zero.any(axis=1), zero.argmax(axis=1) + 1, rounds)
         ops += l * (ALU_INIT + ALU_PACK * b) + l * ALU_TRIAL * ran.mean()
         ops += ALU_ACCEPT * a.sum(axis=1).mean()
-    return ops
+        steps += l * ran.mean()
+    return ops, steps
 
 
 def tf32_peak(dev, stream):
@@ -442,14 +444,23 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, mo, enc = cpu_baseline(w, X)
         if mo.plan == plan:
-            ops = alu_ops_per_vector(enc, mo, w["rounds"])
+            ops, steps = alu_ops_per_vector(enc, mo, w["rounds"])
+            # the step's own instruction ceiling at the quantize kernel's
+            # occupancy (32 warps per SM), B of the plan's longest segment
+            bits = max(mo.kept, key=lambda k: k[1])[2]
+            ceil = P.saq_quantize_step_ceiling(32, bits)
             sm_mhz = clocks.get("sm_mhz") or pk["sm_max_mhz"]
             alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12
             alu = {"bound": "alu", "kernel": "quantize_adjust_pack",
                    "ops_per_vector": ops, "achieved": ops * n / t_caq / 1e12, "peak": alu_peak,
                    "unit": "Tops/s", "frac": ops * n / t_caq / 1e12 / alu_peak,
                    "peak_source": "152 SMs x 128 lanes x %.0f MHz (one op per lane per clock)" % sm_mhz,
-                   "counted_from": "oracle accept statistics of the cpu_baseline sample"}
+                   "counted_from": "oracle accept statistics of the cpu_baseline sample",
+                   "round_lane_steps_per_vector": steps,
+                   "step_ceiling_lane_steps_per_s": ceil,
+                   "frac_of_step_ceiling": steps * n / t_caq / ceil,
+                   "step_ceiling_source": "saq_quantize_step_ceiling(32 warps/SM, B=%d): the "
+                                          "adjustment step on register-resident data" % bits}
 
     if rank == 0:
         cfg = workload_desc(w, args.workload, args.precision, plan, m.code_bytes)

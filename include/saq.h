@@ -363,6 +363,19 @@ saq_status saq_estimate_staged(const saq_model *m, const uint8_t *codes_dev,
 saq_status saq_model_set_basis(saq_model *m, const double *Vt);
 int32_t saq_model_has_basis(const saq_model *m);
 
+/* Instruction ceiling of the code adjustment (diagnostic; no counterpart in
+ * the paper).  Runs the adjustment's own per-coordinate step (Algorithm 1 in
+ * the closed form of saq_encode) on coordinates held in registers, with no
+ * memory traffic, at warps_per_sm resident warps per SM (8, 16, ..., 64;
+ * the quantize kernel runs at 32) and B = bits, on the current device and
+ * the legacy default stream, and writes the lane-steps per second
+ * (coordinate trials of one vector-segment each) to *lane_steps_per_s.
+ * Synchronous.  The quantize kernel's own rate of lane-steps measured
+ * against it shows how much of the step's issue ceiling it reaches.
+ * SAQ_ERR_INVALID on bad arguments. */
+saq_status saq_quantize_step_ceiling(int32_t warps_per_sm, int32_t bits,
+                                     double *lane_steps_per_s);
+
 /* Kernel timing (diagnostic; no counterpart in the paper).  While enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded
  * on its own stream, just before the launch and just after it, so that each

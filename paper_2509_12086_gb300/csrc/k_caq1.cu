@@ -96,16 +96,36 @@ struct LaneState {
     float I, S, I2;
 };
 
+// One coordinate of Algorithm 1 for one lane: returns the coordinate's code
+// after the step and sets `accepted` if it moved.  u = 2c - cmax is formed
+// as a float without a conversion: the bits 0x4B400000 + (2c - cmax) are the
+// float 1.5 * 2^23 + (2c - cmax) exactly (unit spacing there), ubias =
+// 0x4B400000 - cmax; s = sign(T) (+ for T = +0); s*u < cmax is the range
+// check of c + s.
+__device__ __forceinline__ int caq_step(LaneState &L, float x, int c, int ubias, float cmaxf,
+                                        bool &accepted) {
+    const float u = __int_as_float(ubias + 2 * c) - 12582912.f;
+    const float xS = x * L.S;
+    const float T = fmaf(-u, L.I, xS);
+    const uint32_t sgn = __float_as_uint(T) & 0x80000000u;
+    const float su = __uint_as_float(__float_as_uint(u) ^ sgn);
+    if (su < cmaxf && fmaf(fabsf(T), L.I, x * xS) > L.I2) {
+        L.I = fmaf(__uint_as_float(0x40000000u | sgn), x, L.I);
+        L.S = fmaf(4.f, su, L.S + 4.f);
+        L.I2 = L.I * L.I;
+        c = sgn ? c - 1 : c + 1;
+        accepted = true;
+    }
+    return c;
+}
+
 // One round of Algorithm 1 over the lane's segment: coordinates j0 + U ..
 // j0 + 2U - 1 are loaded before j0 .. j0 + U - 1 are processed (a code is only
-// written at its own step, so the prefetched codes are current).  u = 2c -
-// cmax is formed as a float without a conversion: the bits 0x4B400000 +
-// (2c - cmax) are the float 1.5 * 2^23 + (2c - cmax) exactly (unit spacing
-// there); s = sign(T) (+ for T = +0); s*u < cmax is the range check of c + s.
-// With PACK_B = B > 0 the round is the last one: a coordinate's code is final
-// once its own step is done, so the bit-planes (most significant first,
-// 64-bit words) and the exact |u|^2, which the function returns, are built
-// as the round goes.
+// written at its own step, so the prefetched codes are current).  With
+// PACK_B = B > 0 the round is the last one: a coordinate's code is final once
+// its own step is done, so the bit-planes (most significant first, 64-bit
+// words) and the exact |u|^2, which the function returns, are built as the
+// round goes.
 template <int PACK_B>
 __device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t *cp, int len,
                                          int cmax, bool &moved, bool valid, uint64_t *cout,
@@ -119,16 +139,9 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t 
     for (int p = 0; p < NW; ++p) w[p] = 0ull;
     int Si = 0;
     auto step = [&](float x, int c, int j) {
-        const float u = __int_as_float(ubias + 2 * c) - 12582912.f;
-        const float xS = x * L.S;
-        const float T = fmaf(-u, L.I, xS);
-        const uint32_t sgn = __float_as_uint(T) & 0x80000000u;
-        const float su = __uint_as_float(__float_as_uint(u) ^ sgn);
-        if (su < cmaxf && fmaf(fabsf(T), L.I, x * xS) > L.I2) {
-            L.I = fmaf(__uint_as_float(0x40000000u | sgn), x, L.I);
-            L.S = fmaf(4.f, su, L.S + 4.f);
-            L.I2 = L.I * L.I;
-            c = sgn ? c - 1 : c + 1;
+        bool accepted = false;
+        c = caq_step(L, x, c, ubias, cmaxf, accepted);
+        if (accepted) {
             cp[(int64_t)j << 5] = (uint8_t)c;
             moved = true;
         }
@@ -306,6 +319,34 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
     }
 }
 
+// The instruction ceiling of the adjustment: caq_step on coordinates held in
+// registers (no loads or stores), kU per lane, a sign flip per step keeping
+// moves happening; one block of 256 threads per 8 warps of occupancy.
+__global__ void __launch_bounds__(256) k_step_ceiling(int iters, int cmax, float *out) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    float x[kU];
+    int c[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+        x[k] = (float)((tid * 7 + k * 13) % 31) * 0.03f - 0.45f;
+        c[k] = (tid + k) % (cmax + 1);
+    }
+    LaneState L{10.f, 200.f, 100.f};
+    const int ubias = 0x4B400000 - cmax;
+    const float cmaxf = (float)cmax;
+    int moves = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kU; ++k) {
+            bool accepted = false;
+            c[k] = caq_step(L, x[k], c[k], ubias, cmaxf, accepted);
+            moves += accepted ? 1 : 0;
+            x[k] = -x[k];
+        }
+    }
+    out[tid] = L.I + L.S + (float)moves + (float)c[0];
+}
+
 // v_max of every (row, kept segment) of interleaved rows: one warp per (group
 // of 32 rows, kept segment), lane = row.
 __global__ void __launch_bounds__(256)
@@ -370,6 +411,39 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
     return SAQ_OK;
+}
+
+saq_status step_ceiling(int warps_per_sm, int bits, double *lane_steps_per_s) {
+    int dev = 0, sms = 0;
+    SAQ_CUDA_CHECK(cudaGetDevice(&dev));
+    SAQ_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * (warps_per_sm / 8);
+    const int iters = 2000;
+    float *out = nullptr;
+    SAQ_CUDA_CHECK(scratch_alloc((void **)&out, sizeof(float) * (size_t)blocks * 256, 0));
+    cudaEvent_t a = nullptr, b = nullptr;
+    saq_status st = SAQ_OK;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        st = set_error(SAQ_ERR_CUDA, "event creation failed");
+    } else {
+        const int cmax = (1 << bits) - 1;
+        k_step_ceiling<<<blocks, 256>>>(iters / 4, cmax, out);  // warm-up
+        cudaEventRecord(a, 0);
+        k_step_ceiling<<<blocks, 256>>>(iters, cmax, out);
+        cudaEventRecord(b, 0);
+        note_launches(2);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess || ms <= 0.f)
+            st = set_error(SAQ_ERR_CUDA, "step-ceiling measurement failed");
+        else
+            *lane_steps_per_s = (double)blocks * 256.0 * iters * kU / (ms * 1e-3);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFreeAsync(out, 0);
+    cudaStreamSynchronize(0);
+    return st;
 }
 
 saq_status launch_seg_vmax(const saq_model *m, const float *Oi, int64_t n, float *vmax,

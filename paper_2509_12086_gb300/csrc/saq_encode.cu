@@ -379,6 +379,16 @@ saq_status saq_estimate_dist(const saq_model *m, const uint8_t *codes_dev,
     return st;
 }
 
+saq_status saq_quantize_step_ceiling(int32_t warps_per_sm, int32_t bits,
+                                     double *lane_steps_per_s) {
+    clear_error();
+    if (!lane_steps_per_s) return set_error(SAQ_ERR_INVALID, "NULL output");
+    if (warps_per_sm < 8 || warps_per_sm > 64 || warps_per_sm % 8 != 0)
+        return set_error(SAQ_ERR_INVALID, "warps_per_sm must be 8, 16, ..., 64");
+    if (bits < 1 || bits > 8) return set_error(SAQ_ERR_INVALID, "bits outside 1..8");
+    return step_ceiling(warps_per_sm, bits, lane_steps_per_s);
+}
+
 saq_status saq_estimate_staged(const saq_model *m, const uint8_t *codes_dev,
                                const float *factors_dev, int64_t n, const float *Q_dev, int64_t nq,
                                float m_conf, float *bounds_dev, void *stream) {

@@ -147,6 +147,9 @@ saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
 saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
                        const float *vmax, uint8_t *codes, float *factors, cudaStream_t s);
 // vmax of every (row, kept segment) from interleaved rows Oi (k_caq1.cu).
+// Lane-steps per second of the adjustment step on register-resident data
+// (saq_quantize_step_ceiling).
+saq_status step_ceiling(int warps_per_sm, int bits, double *lane_steps_per_s);
 saq_status launch_seg_vmax(const saq_model *m, const float *Oi, int64_t n, float *vmax,
                            cudaStream_t s);
 // Row-major O -> interleaved Oi.

@@ -37,3 +37,14 @@ def test_kernel_times_cover_the_encode():
     P.saq_kernel_timing(True)
     assert all(v == (0.0, 0) for v in P.saq_kernel_times().values())
     P.saq_kernel_timing(False)
+
+
+def test_step_ceiling_rises_with_occupancy():
+    """saq_quantize_step_ceiling: the adjustment step on register-resident
+    data; more resident warps hide more of its dependency chain."""
+    torch.cuda.set_device(0)
+    r8 = P.saq_quantize_step_ceiling(8, 4)
+    r32 = P.saq_quantize_step_ceiling(32, 4)
+    assert r8 > 0 and r32 > 1.2 * r8
+    with pytest.raises(P.SaqError):
+        P.saq_quantize_step_ceiling(12, 4)
