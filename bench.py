@@ -413,7 +413,8 @@ def run_ours(args):
             m.set_precision(prec)
             for _ in range(2):
                 step()
-            t = time_events(step, max(3, args.steps // 2), stream)
+            barrier(world)
+            t = max_over_ranks(world, time_events(step, max(3, args.steps // 2), stream))
             forms[prec] = {"value": n * world / t, "unit": UNIT, "ms_per_step": t * 1e3,
                            "tensor_cores": m.tensor_cores}
         m.set_precision(args.precision)
