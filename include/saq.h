@@ -158,7 +158,7 @@ saq_status saq_encode(const saq_model *m, const float *X_dev, int64_t n,
 
 /*
  * Same as saq_encode, with host buffers: the rows are copied to the device
- * in chunks of about 512 MB, encoded and the codes and factors copied back,
+ * in chunks of about 128 MB, encoded and the codes and factors copied back,
  * through three staging slots, with the copy-in of the next chunk and the
  * copy-out of the previous one (on two streams of their own) overlapping the
  * encode of the current one.  Page-locked host memory is strongly

@@ -360,10 +360,10 @@ def test_c1_staged_estimator_parity(c1):
 
 
 def test_host_path_several_chunks_equals_device_encode():
-    """saq_encode_host stages about 512 MB of rows per chunk in three slots:
-    at d = 4096 that is 32,768 rows, so 100,000 rows run three full chunks
-    and a partial one and reuse a slot; every output must equal the device
-    encode of the same rows."""
+    """saq_encode_host stages about 128 MB of rows per chunk in three slots:
+    at d = 4096 that is 8,192 rows, so 100,000 rows run twelve full chunks
+    and a partial one and reuse every slot; every output must equal the
+    device encode of the same rows."""
     torch.cuda.set_device(0)
     d = 4096
     X = synth.power_law(100_000, d, 0.6, device="cuda")
