@@ -87,7 +87,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -401,9 +401,16 @@ def run_ours(args):
             m.encode_host(Xh, ch, fh)
         dt = (time.perf_counter() - t0) / args.e2e_steps
         dt = max_over_ranks(world, dt)
+        # the host link's own rate on this machine: the same rows copied alone
+        scratch = torch.empty((ne, d), dtype=torch.float32, device=dev)
+        scratch.copy_(Xh, non_blocking=True)
+        t_copy = time_events(lambda: scratch.copy_(Xh, non_blocking=True), 3, stream)
+        del scratch
+        h2d_gbs = ne * d * 4 / t_copy / 1e9
         e2e = {"value": ne * world / dt, "unit": UNIT, "h2d_bytes_per_step": ne * d * 4,
                "d2h_bytes_per_step": ne * (m.code_bytes + 4 * m.factor_count),
-               "rows_per_step": ne}
+               "rows_per_step": ne, "h2d_gbs_measured": h2d_gbs,
+               "frac_of_copy_in_bound": (ne / dt) / (ne / t_copy)}
         del Xh, ch, fh
 
     # the precision forms on the same batch (BF16 / FP8 projection, FP32 quantization)
