@@ -404,3 +404,19 @@ def test_more_kept_segments_than_supported_is_an_error():
     X = torch.randn(64, d, device="cuda")
     with pytest.raises(P.SaqError):
         m.encode(X)
+
+
+@pytest.mark.parametrize("prec", precisions())
+def test_odd_segment_lengths(prec):
+    """Segments of 5, 13, 70, 37 and 3 coordinates at offsets that are no
+    multiple of 8: the partial batches of the initial pass, the rounds and
+    the packing, a segment spanning two 64-bit words, and projection blocks
+    that straddle segment ends."""
+    plan = [(0, 5, 4), (5, 13, 6), (18, 70, 3), (88, 37, 2), (125, 3, 1)]
+    mo = _random_model(128, plan, seed=5)
+    rng = np.random.default_rng(17)
+    X = (rng.standard_normal((1000, 128)) * np.linspace(1, 0.1, 128)).astype(np.float32)
+    eo = O.encode(X, mo, rounds=6)
+    m = lib_model(mo, prec)
+    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(), agree_min=0.999)
