@@ -71,7 +71,7 @@ template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage
     static constexpr int BK = 32, STAGES = 3, NA = 2, XBOX = 1, TMEM = 512;
 };
 template <> struct Cfg<kBF16> {
-    static constexpr int BK = 32, STAGES = 4, NA = 1, XBOX = 1, TMEM = 256;
+    static constexpr int BK = 32, STAGES = 5, NA = 1, XBOX = 1, TMEM = 256;
 };
 template <> struct Cfg<kFP8> {  // 64 E4M3 per row per stage
     static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2, TMEM = 256;
@@ -90,9 +90,13 @@ template <int MODE> constexpr uint32_t b_offset() {
 static_assert(Cfg<kSplit>::STAGES * stage_bytes<kSplit>() > 228u * 1024u / 2u,
               "two split-mode CTAs per SM would share 512 TMEM columns");
 // dynamic shared memory: stages, barriers and the row-norm halves, -c*s
-template <int MODE> uint32_t smem_bytes(int dpad) {
+template <int MODE> constexpr uint32_t smem_bytes(int dpad) {
     return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + 640 + 4u * (uint32_t)dpad;
 }
+// every form fits the 227 KB a CTA may opt into at the largest supported d (6144)
+static_assert(smem_bytes<kSplit>(6144) <= 227u * 1024u && smem_bytes<kBF16>(6144) <= 227u * 1024u &&
+                  smem_bytes<kFP8>(6144) <= 227u * 1024u,
+              "stages exceed the dynamic shared memory of one CTA");
 
 // ------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
