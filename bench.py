@@ -179,10 +179,11 @@ def workload_desc(w, name, precision, plan, code_bytes):
             "l2": "inputs (%.2f GB) larger than L2 (129 MB): no flush" % (w["n"] * w["d"] * 4 / 1e9)}
 
 
-def cpu_baseline(w, X_dev, target_s=12.0, chunk=100000):
+def cpu_baseline(w, X_dev, target_s=12.0, chunk=100000, one_core_s=3.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of
     the same workload: the rows it encodes in about `target_s` seconds, in
-    chunks of `chunk` rows (model fitted on 50,000 rows, not timed)."""
+    chunks of `chunk` rows (model fitted on 50,000 rows, not timed); beside it
+    the same oracle on one core, for about `one_core_s` seconds."""
     import oracle as O
     fit_rows = min(w["n"], 50000)
     Xf = X_dev[:fit_rows].cpu().numpy()
@@ -201,9 +202,45 @@ def cpu_baseline(w, X_dev, target_s=12.0, chunk=100000):
         dt += time.perf_counter() - t0
         if enc is None:
             enc = e
-    return {"value": ns / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+    cores = O.max_threads()
+    ns1 = int(min(ns, max(200, one_core_s / max(per * cores, 1e-9))))
+    one = cpu_baseline_one_core(mo, X_dev[:ns1].cpu().numpy(), w["rounds"])
+    return {"value": ns / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d rows of the workload in chunks of %d (oracle fit on %d rows, not timed): "
-                      "FP64 projection + CAQ + factors, %.1f s" % (ns, chunk, fit_rows, dt)}, mo, enc
+                      "FP64 projection + CAQ + factors, %.1f s" % (ns, chunk, fit_rows, dt),
+            "one_core": one}, mo, enc
+
+
+_ONE_CORE = r"""
+import os, pickle, sys, time
+os.sched_setaffinity(0, {min(os.sched_getaffinity(0))})
+sys.path.insert(0, sys.argv[1])
+import oracle as O
+with open(sys.argv[2], "rb") as f:
+    mo, X, rounds = pickle.load(f)
+t0 = time.perf_counter()
+O.encode(X, mo, rounds=rounds, nthreads=1)
+print(time.perf_counter() - t0, O.max_threads())
+"""
+
+
+def cpu_baseline_one_core(mo, X, rounds):
+    """The same oracle on one core: a child process pinned to one CPU, with one
+    OpenMP thread and one BLAS thread, on the first rows of the sample."""
+    import pickle
+    import tempfile
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "sample.pkl")
+        with open(path, "wb") as f:
+            pickle.dump((mo, X, rounds), f)
+        out = subprocess.run([sys.executable, "-c", _ONE_CORE, ROOT, path], env=env,
+                             capture_output=True, text=True, timeout=600, check=True)
+    dt, threads = out.stdout.split()[-2:]
+    dt = float(dt)
+    return {"value": X.shape[0] / dt, "unit": UNIT, "cores": 1, "omp_threads": int(threads),
+            "sample": "%d rows of the workload, one pinned CPU, one OpenMP and one BLAS thread, "
+                      "%.1f s" % (X.shape[0], dt)}
 
 
 # Algorithmic lane operations of quantize / adjust / pack (Eq. find_nearest_code,
