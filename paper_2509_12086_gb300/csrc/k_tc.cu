@@ -89,9 +89,16 @@ template <int MODE> constexpr uint32_t b_offset() {
 // its own): its stages alone take more than half of the 228 KB of an SM.
 static_assert(Cfg<kSplit>::STAGES * stage_bytes<kSplit>() > 228u * 1024u / 2u,
               "two split-mode CTAs per SM would share 512 TMEM columns");
-// dynamic shared memory: stages, barriers and the row-norm halves, -c*s
+// barriers (full, conv, empty per stage; the accumulator's), the TMEM address
+// and the abort flag, ahead of the row-norm halves
+constexpr uint32_t kBarArea = 256;
+template <int MODE> constexpr uint32_t bar_bytes() { return 3u * 8u * Cfg<MODE>::STAGES + 8u + 8u; }
+static_assert(bar_bytes<kSplit>() <= kBarArea && bar_bytes<kBF16>() <= kBarArea &&
+                  bar_bytes<kFP8>() <= kBarArea,
+              "barriers overflow their shared-memory area");
+// dynamic shared memory: stages, barriers, the row-norm halves, -c*s
 template <int MODE> constexpr uint32_t smem_bytes(int dpad) {
-    return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + 640 + 4u * (uint32_t)dpad;
+    return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + kBarArea + 512 + 4u * (uint32_t)dpad;
 }
 // every form fits the 227 KB a CTA may opt into at the largest supported d (6144)
 static_assert(smem_bytes<kSplit>(6144) <= 227u * 1024u && smem_bytes<kBF16>(6144) <= 227u * 1024u &&
@@ -284,8 +291,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
     uint64_t *accf = empty + C::STAGES;
     uint32_t *tmem_slot = (uint32_t *)(accf + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    float *nrm_half = (float *)(smem + C::STAGES * SB + 128);   // 128 floats
-    float *mcs = (float *)(smem + C::STAGES * SB + 128 + 512);  // nkb * BK floats
+    float *nrm_half = (float *)(smem + C::STAGES * SB + kBarArea);        // 128 floats
+    float *mcs = (float *)(smem + C::STAGES * SB + kBarArea + 512);       // nkb * BK floats
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tile = blockIdx.x / npass;
