@@ -41,9 +41,9 @@ UNIT = "vectors/s"
 # traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "ab21f74857ae32b4603509411b43a7ad1847607e",
+    "projection": {"src": "k_tc.cu", "sha1": "68c398affe0ff58904090088fa9d57cb5a815864",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258.210560e6 + 213.303552e6) / 65536},
+                   "bytes_per_row": (258.269696e6 + 212.482816e6) / 65536},
     "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ffb094df723d5f82f42d644a9eb4cc3d9a4c3090",
                              "workload": "c2_d960", "precision": "fp32",
                              "bytes_per_row": (1981.363e6 + 287.469824e6) / 65536},
@@ -547,8 +547,9 @@ def serving_run(args, dev):
     collections (d = 128 / 960 at 4 b/dim, d = 1536 at 2 b/dim, alpha 0.8),
     requests of log-uniform size in [1, 65536] rows (2M vectors in all).  The
     service's capacity on this mix is measured first (all requests submitted
-    at once, copies included); then the same requests arrive as a Poisson
-    stream at a load factor of that capacity.  HBM budget 40 GB."""
+    at once, copies included, median of three passes); then the same requests
+    arrive as a Poisson stream at a load factor of that capacity, three runs
+    per load factor.  HBM budget 40 GB."""
     rng = np.random.default_rng(2024)
     specs = [(128, 4.0), (960, 4.0), (1536, 2.0)]
     models = []
@@ -573,15 +574,15 @@ def serving_run(args, dev):
     for t in [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs[:30]]:
         svc.wait(t, timeout_ms=120000)
     # capacity of the service on this request mix: everything submitted at
-    # once, the better of two passes
-    sat_s = float("inf")
-    for _ in range(2):
+    # once, the median of three passes
+    sat = []
+    for _ in range(3):
         t0 = time.perf_counter()
         tk = [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs]
         for t in tk:
             svc.wait(t, timeout_ms=120000)
-        sat_s = min(sat_s, time.perf_counter() - t0)
-    capacity = sum(sizes) / sat_s
+        sat.append(time.perf_counter() - t0)
+    capacity = sum(sizes) / float(np.median(sat))
     # Poisson arrivals at load factors rho of that capacity (the headline
     # figures are those of --ingest-load; 0.5 and 0.95 are reported beside)
     def poisson(rho, seed):
@@ -604,8 +605,15 @@ def serving_run(args, dev):
                 "p50_ms": float(np.percentile(lats, 50) * 1e3),
                 "p99_ms": float(np.percentile(lats, 99) * 1e3), "max_ms": float(lats.max() * 1e3),
                 "batches": int(svc.stats()["batches"] - b0)}
-    head = poisson(args.ingest_load, 2025)
-    others = {("%.2f" % rho): poisson(rho, 2026 + k)
+    # each load factor three times (a run lasts 0.05-0.1 s, so one hiccup of
+    # the host can decide it): the run with the median p99, and all three
+    def median_run(rho, seed):
+        runs = sorted((poisson(rho, seed + 100 * k) for k in range(3)), key=lambda r: r["p99_ms"])
+        out = dict(runs[1])
+        out["runs_p50_p99_ms"] = [[r["p50_ms"], r["p99_ms"]] for r in runs]
+        return out
+    head = median_run(args.ingest_load, 2025)
+    others = {("%.2f" % rho): median_run(rho, 2026 + k)
               for k, rho in enumerate((0.5, 0.95)) if abs(rho - args.ingest_load) > 1e-9}
     svc.close()
     out = {"requests": len(sizes), "vectors": int(sum(sizes)), "saturation_vectors_per_s": capacity}
