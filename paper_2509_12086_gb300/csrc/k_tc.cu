@@ -16,10 +16,16 @@
 //               alternate K blocks (two blocks in conversion at once); in a
 //               group one thread per tile row reads the staged X values,
 //               centres and scales them with one FMA against -c*s kept in
-//               shared memory, converts them into the A operand(s) (UMMA
-//               K-major, 64-byte rows, 64-byte swizzle) and accumulates
-//               |x - c|^2; after the K loop each warp drains its TMEM lane
-//               quadrant for alternate 16-column chunks with tcgen05.ld.
+//               shared memory, converts them into the A operand(s) and
+//               accumulates |x - c|^2; after the K loop each warp drains its
+//               TMEM lane quadrant for alternate 32-column blocks with
+//               tcgen05.ld.  The split form writes its A tiles to shared
+//               memory (UMMA K-major, 64-byte rows, 64-byte swizzle); the BF16
+//               and FP8 forms write each row's A values to TMEM with
+//               tcgen05.st (one 16-column buffer per stage beside the
+//               accumulator) and their MMAs read A from there, which takes
+//               the A tile's write and its reads by the MMAs off the shared
+//               memory ports.
 // Operand rows are 64 bytes per stage (32 FP16/BF16 or 64 E4M3 values), so
 // three or more stages fit in shared memory.
 // Precision modes:
@@ -66,19 +72,27 @@ constexpr uint32_t kXBox = 16384;   // 128 rows x 128 bytes of staged FP32
 constexpr uint32_t kATile = 8192;   // 128 rows x 64 bytes
 constexpr uint32_t kBTile = 16384;  // 256 rows x 64 bytes
 
+// Per stage: XBOX staged X boxes, NA A-operand tiles in shared memory (0: the
+// A operand of the stage lives in TMEM), NB W-operand tiles.
 template <int MODE> struct Cfg;
-template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage
-    static constexpr int BK = 32, STAGES = 3, NA = 2, XBOX = 1, TMEM = 512;
+template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage, A hi/lo in shared memory
+    static constexpr int BK = 32, STAGES = 3, NA = 2, NB = 2, XBOX = 1, TMEM = 512;
 };
-template <> struct Cfg<kBF16> {
-    static constexpr int BK = 32, STAGES = 5, NA = 1, XBOX = 1, TMEM = 256;
+template <> struct Cfg<kBF16> {  // 32 BF16 per row per stage, A in TMEM
+    static constexpr int BK = 32, STAGES = 6, NA = 0, NB = 1, XBOX = 1, TMEM = 512;
 };
-template <> struct Cfg<kFP8> {  // 64 E4M3 per row per stage
-    static constexpr int BK = 64, STAGES = 3, NA = 1, XBOX = 2, TMEM = 256;
+template <> struct Cfg<kFP8> {  // 64 E4M3 per row per stage, A in TMEM
+    static constexpr int BK = 64, STAGES = 4, NA = 0, NB = 1, XBOX = 2, TMEM = 512;
 };
+// TMEM column of the first A buffer of the forms that keep A in TMEM: one
+// buffer of 16 columns (64 bytes of a row) per stage, after the accumulator
+constexpr uint32_t kTA = 256;
+static_assert(kTA + 16u * Cfg<kBF16>::STAGES <= 512u && kTA + 16u * Cfg<kFP8>::STAGES <= 512u,
+              "A buffers exceed the TMEM allocation");
 
 template <int MODE> constexpr uint32_t stage_bytes() {
-    return (uint32_t)Cfg<MODE>::XBOX * kXBox + (uint32_t)Cfg<MODE>::NA * (kATile + kBTile);
+    return (uint32_t)Cfg<MODE>::XBOX * kXBox + (uint32_t)Cfg<MODE>::NA * kATile +
+           (uint32_t)Cfg<MODE>::NB * kBTile;
 }
 template <int MODE> constexpr uint32_t a_offset() { return (uint32_t)Cfg<MODE>::XBOX * kXBox; }
 template <int MODE> constexpr uint32_t b_offset() {
@@ -87,8 +101,10 @@ template <int MODE> constexpr uint32_t b_offset() {
 // A CTA that allocates all 512 TMEM columns must be alone on its SM (an
 // allocation beyond the free columns waits for a co-resident CTA to free
 // its own): its stages alone take more than half of the 228 KB of an SM.
-static_assert(Cfg<kSplit>::STAGES * stage_bytes<kSplit>() > 228u * 1024u / 2u,
-              "two split-mode CTAs per SM would share 512 TMEM columns");
+static_assert(Cfg<kSplit>::STAGES * stage_bytes<kSplit>() > 228u * 1024u / 2u &&
+                  Cfg<kBF16>::STAGES * stage_bytes<kBF16>() > 228u * 1024u / 2u &&
+                  Cfg<kFP8>::STAGES * stage_bytes<kFP8>() > 228u * 1024u / 2u,
+              "two CTAs per SM would share 512 TMEM columns");
 // barriers (full, conv, empty per stage; the accumulator's), the TMEM address
 // and the abort flag, ahead of the row-norm halves
 constexpr uint32_t kBarArea = 256;
@@ -219,6 +235,34 @@ __device__ __forceinline__ void umma(uint32_t dtm, uint64_t a, uint64_t b, uint3
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     }
 }
+// the same with the A operand in TMEM (column address `atm`, 128 lanes)
+template <int MODE>
+__device__ __forceinline__ void umma_ta(uint32_t dtm, uint32_t atm, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+    if (MODE == kFP8) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+            "r"(atm), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+            "r"(atm), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+// 16 consecutive 32-bit TMEM columns of the warp's lane quadrant, one word per
+// column from each thread (its own lane), and the wait for them
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&w)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta),
+        "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]),
+        "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -326,7 +370,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
     if (warp == 0) {
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmx) : "memory");
-            const uint32_t tx = (uint32_t)C::XBOX * kXBox + (uint32_t)C::NA * (uint32_t)np * 64u;
+            const uint32_t tx = (uint32_t)C::XBOX * kXBox + (uint32_t)C::NB * (uint32_t)np * 64u;
             // X boxes kPrefetch K blocks ahead are pulled into L2, so that the
             // stage loads wait on L2 rather than on HBM
             for (int kb = C::STAGES; kb < kPrefetch && kb < nkb; ++kb)
@@ -345,7 +389,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                 uint8_t *bs = st + b_offset<MODE>();
                 const int64_t wo = ((int64_t)pass * nkb + kb) * np * 64;
                 bulk_load(bs, wt0 + wo, (uint32_t)np * 64u, &full[s]);
-                if (C::NA == 2) bulk_load(bs + kBTile, wt1 + wo, (uint32_t)np * 64u, &full[s]);
+                if (C::NB == 2) bulk_load(bs + kBTile, wt1 + wo, (uint32_t)np * 64u, &full[s]);
                 if (kb + kPrefetch < nkb)
 #pragma unroll
                     for (int b = 0; b < C::XBOX; ++b)
@@ -377,6 +421,11 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
                     const uint64_t off = (uint64_t)(kk * 2);
+                    if (C::NA == 0) {  // A of the stage in TMEM, 8 columns per K step
+                        umma_ta<MODE>(tmem, tmem + kTA + 16u * (uint32_t)s + 8u * (uint32_t)kk,
+                                      b0 + off, idesc, (kb | kk) != 0);
+                        continue;
+                    }
                     umma<MODE>(tmem, a0 + off, b0 + off, idesc, (kb | kk) != 0);
                     if (C::NA == 2) {
                         umma<MODE>(tmem + kAcc2, a0 + off, b1 + off, idesc, (kb | kk) != 0);
@@ -395,6 +444,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
         const int q = warp & 3;
         const int r = q * 32 + lane;
         const int h = (warp - 2) >> 2;
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);  // the warp's TMEM lane quadrant
         const bool row_ok = row0 + r < n;
         float nrm = 0.f;
         bool ok = true;
@@ -416,6 +466,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
             uint8_t *st = smem + s * SB;
             uint8_t *a0 = st + a_offset<MODE>();
             const float *mk = mcs + kb * C::BK;
+            uint32_t wa[16];  // A row of the stage for the forms that keep A in TMEM
             if (MODE == kFP8) {
                 // 4 chunks of 16 E4M3 (64 values) per thread, from the two staged boxes
 #pragma unroll
@@ -438,7 +489,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                             make_float2(y2, y3), __NV_SATFINITE, __NV_E4M3);
                         w[e] = (uint32_t)lo | ((uint32_t)hi << 16);
                     }
-                    *reinterpret_cast<uint4 *>(a0 + swz64(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 16i + 4e .. + 3
                 }
             } else {
                 uint8_t *a1 = a0 + kATile;
@@ -461,7 +513,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             w[e] = pack_b2(__floats2bfloat162_rn(y[2 * e], y[2 * e + 1]));
-                        *reinterpret_cast<uint4 *>(a0 + swz64(r, ac)) = make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 8i + 2e, + 1
                     } else {
                         uint32_t wh[4], wl[4];
 #pragma unroll
@@ -478,7 +531,15 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                     }
                 }
             }
-            fence_proxy_async();
+            if (C::NA == 0) {
+                // TMEM column c of the buffer holds the row's values of K
+                // offsets c * (4 / element bytes) upward, lowest in the low bits
+                tmem_st16(tq + kTA + 16u * (uint32_t)s, wa);
+                tmem_st_wait();
+                tc_fence_before();
+            } else {
+                fence_proxy_async();
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv[s]);
         }
@@ -500,7 +561,6 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
             const bool want_vmax = il && vmax != nullptr;
             float *vgrp = want_vmax ? vmax + (((row0 + r) >> 5) * (int64_t)segc.nk << 5) + lane
                                     : nullptr;
-            const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
             int si = 0;
             float mx = 0.f;
             // 32-column blocks, alternating between the two threads of a row; a
