@@ -522,7 +522,10 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": max(3, args.warmup),
                "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+               # projection operands of the form (FP32 accumulation; quantize,
+               # adjust and factors in FP32 in every form)
+               "dtype": {"bf16": "bf16", "fp8": "e4m3"}.get(args.precision, "f32"),
                "config": cfg, "roofline": roof,
                "kernels_ms_per_step": {"projection": t_proj * 1e3,
                                        "quantize_adjust_pack": t_caq * 1e3,
