@@ -418,6 +418,12 @@ def run_ours(args):
     caq_roof["traffic"] = traffic_per_launch("quantize_adjust_pack", args.workload, args.precision,
                                              n / max(l_q / args.steps, 1))
     caq_roof["algorithmic_bytes_per_launch"] = caq_bytes / max(l_q / args.steps, 1)
+    if caq_roof["traffic"] is not None:
+        # the DRAM bytes the launches actually move (each adjustment round
+        # re-reads the segment's rows and codes) over their time
+        gbs = caq_roof["traffic"] * (l_q / args.steps) / t_caq / 1e9
+        caq_roof["dram_traffic_gbs"] = gbs
+        caq_roof["dram_traffic_frac"] = gbs / pk["hbm_gbs"]
     if t_proj >= t_caq:
         roof, dom = proj_roof, "projection"
     else:
@@ -518,7 +524,9 @@ def run_ours(args):
             roof = dict(alu)
             roof["traffic"] = caq_roof["traffic"]
             roof["hbm_view"] = {k: caq_roof[k] for k in ("achieved", "peak", "unit", "frac",
-                                                          "algorithmic_bytes_per_launch")}
+                                                          "algorithmic_bytes_per_launch",
+                                                          "dram_traffic_gbs", "dram_traffic_frac")
+                                if k in caq_roof}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": max(3, args.warmup),
                "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
