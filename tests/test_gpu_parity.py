@@ -284,6 +284,42 @@ def test_tensor_core_projection_ragged(n, d, plan):
     assert rel.max() <= 5e-6
 
 
+@pytest.mark.parametrize("prec,u", [("bf16", 2.0 ** -8), ("fp8", 2.0 ** -4)])
+@pytest.mark.parametrize("n,d,plan", [
+    (1, 128, [(0, 64, 5), (64, 64, 3)]),
+    (300, 200, [(0, 64, 8), (64, 72, 3), (136, 32, 1), (168, 32, 0)]),
+    (1000, 960, [(0, 64, 8), (64, 192, 5), (256, 256, 4), (512, 448, 3)]),
+])
+def test_precision_form_projection_ragged(prec, u, n, d, plan):
+    """The BF16 / FP8 projection (A operand in TMEM) on ragged rows, a ragged
+    K tail (d = 200 pads to 224 for BF16's 32-value K blocks, to 256 for FP8's
+    64) and ragged columns, against the FP64 projection.  Rounding both
+    operands to a format of unit roundoff u (BF16 2^-8, E4M3 2^-4; the scales
+    are powers of two) bounds each output by |o_i - o~_i| <= (2u + u^2)
+    sum_k |w_ik| |y_k| <= (2u + u^2) |w_i| |y| with |w_i| = 1 (orthonormal
+    rows of W) and y = x - c.  The interleaved layout the encode uses holds
+    the same values."""
+    mo = _random_model(d, plan, seed=d)
+    rng = np.random.default_rng(n + d)
+    X = (rng.standard_normal((n, d)) * np.linspace(1, 0.05, d)).astype(np.float32)
+    m = lib_model(mo, prec)
+    assert m.tensor_cores
+    Xd = torch.from_numpy(X).cuda()
+    Ol, _ = m.project(Xd)
+    Oi, _ = m.project_interleaved(Xd)
+    m.check_device()
+    Oo, n2o = O.project(X, mo)
+    rel = np.abs(Ol.cpu().numpy().astype(np.float64) - Oo) / np.sqrt(n2o)[:, None]
+    bound = 2 * u + u * u
+    assert rel.max() <= bound * 1.001, (rel.max(), bound)
+    # typical errors sit far below the worst case (a misplaced operand gives O(1))
+    assert rel.mean() <= bound / 8, (rel.mean(), bound)
+    dk = mo.d_kept
+    g = (n + 31) // 32
+    Ore = Oi.view(g, dk, 32).permute(0, 2, 1).reshape(g * 32, dk)[:n]
+    assert torch.equal(Ore, Ol)
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
 def test_precision_forms_error_bounded(c1, prec):
     """BF16 / FP8 projection (quantization and adjustment stay FP32): codes
