@@ -325,8 +325,9 @@ def test_precision_forms_error_bounded(c1, prec):
     """BF16 / FP8 projection (quantization and adjustment stay FP32): codes
     differ from the oracle's where the projection error crosses a decision,
     so only the error statistics are bounded.  The projection adds its own
-    error energy: operand rounding of 2^-9 (BF16) or 2^-4 (E4M3) relative on
-    both operands gives about 3e-6 (BF16) or 2.6e-3 (FP8) of |x - c|^2, so the
+    error energy: rounding both operands to unit roundoff u (BF16 2^-8, E4M3
+    2^-4; uniform rounding errors of variance u^2/3 each) gives about
+    2u^2/3 = 1e-5 (BF16) or 2.6e-3 (FP8) of |x - c|^2, so the
     mean quantization error may exceed the oracle's by 10% (BF16) or by an
     absolute 0.01 (FP8, 4x the budget); the estimator error stays within 2x
     (BF16) or 4x (FP8) of the oracle's."""
