@@ -58,3 +58,31 @@ def test_alu_count_follows_rounds_and_accepts():
                 + bench.ALU_ACCEPT * np.array([4, 0]).mean())
     assert steps == want_steps
     assert abs(ops - want_ops) < 1e-9
+
+
+def test_one_core_baseline_runs_the_oracle_on_one_thread():
+    """The one-core figure beside the all-core CPU baseline: a child process
+    pinned to one CPU encodes the given rows with the oracle on one OpenMP
+    thread and reports their rate."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((2000, 64)).astype(np.float32)
+    mo = O.fit(X, 4.0)
+    one = bench.cpu_baseline_one_core(mo, X[:300], 2)
+    assert one["cores"] == 1 and one["omp_threads"] == 1
+    assert one["value"] > 0 and "300 rows" in one["sample"]
+
+
+def test_a_failing_one_core_child_is_reported(monkeypatch):
+    """The all-core baseline still comes back when the one-core child fails;
+    the failure is named in its field."""
+    import subprocess
+    import torch
+
+    def fail(*args, **kwargs):
+        raise subprocess.CalledProcessError(1, "child")
+
+    monkeypatch.setattr(bench, "cpu_baseline_one_core", fail)
+    X = torch.from_numpy(np.random.default_rng(6).standard_normal((3000, 64)).astype(np.float32))
+    cpu, mo, enc = bench.cpu_baseline({"n": 3000, "avg_bits": 4.0, "rounds": 2}, X, target_s=0.2)
+    assert cpu["value"] > 0 and cpu["kind"] == "oracle"
+    assert cpu["one_core"]["value"] is None and "CalledProcessError" in cpu["one_core"]["error"]
