@@ -32,27 +32,30 @@ static double objective(double dot, double sq, double norm_o) {
 }
 
 /*
- * Quantize one segment o[0..len) with B bits (1 <= B <= 8) and adjust the
- * code for `rounds` rounds (Algorithm 1).
- *
- * Outputs:
- *   code[len]          final codes c_a in [0, 2^B - 1]
- *   *norm_out          |o|
- *   *cos_out           L(o_bar_a, o), the cosine between the adjusted quantized
- *                      vector and o (the second stored factor, Sec. 3.1 end)
- *   accepts[rounds]    number of accepted moves in each round
- *   *min_trial_margin  min over all in-range trials of |L(x') - L(x)|
- *   *min_init_margin   min over coordinates of the distance from o[i] to the
- *                      nearest interior interval boundary of the initial grid,
- *                      divided by |o| (how far o[i] must move, relative to the
- *                      segment norm, to change its initial code)
- *   *init_cos          L(o_bar, o) of the initial (unadjusted) code
- * Returns the number of accepted moves in total.
+ * Algorithm 1 on one segment, shared by the plain entry point below and by
+ * the replay that records every decision (saq_oracle_caq_trace).  The trace
+ * outputs may be NULL; they only observe the run and change nothing in it:
+ *   codes_after[(r + 1) * len + i]  code of coordinate i after round r
+ *                                   (row 0: the initial code)
+ *   init_margin[i]                  distance of o[i] to the nearest interior
+ *                                   interval boundary of the initial grid,
+ *                                   divided by |o| (as *min_init_margin)
+ *   dplus[r * len + i], dminus[r * len + i]
+ *                                   L(x + Delta e_i) - L(x) and
+ *                                   L(x - Delta e_i) - L(x) evaluated at the
+ *                                   state x reached when round r arrives at
+ *                                   coordinate i, before its +Delta trial;
+ *                                   -INFINITY where the move leaves
+ *                                   [-vmax, vmax].  dplus is the algorithm's
+ *                                   own +Delta trial; dminus is its -Delta
+ *                                   trial whenever +Delta was rejected.
  */
-int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
-                           uint8_t *code, double *norm_out, double *cos_out,
-                           int *accepts, double *min_trial_margin,
-                           double *min_init_margin, double *init_cos) {
+static int caq_run(const double *o, int len, int B, int rounds,
+                   uint8_t *code, double *norm_out, double *cos_out,
+                   int *accepts, double *min_trial_margin,
+                   double *min_init_margin, double *init_cos,
+                   uint8_t *codes_after, double *init_margin,
+                   double *dplus, double *dminus) {
     int i, r, total = 0;
     const int cmax = (1 << B) - 1;
     double vmax = 0.0, nrm2 = 0.0;
@@ -71,6 +74,12 @@ int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
         *norm_out = 0.0;
         *cos_out = 1.0;
         *init_cos = 1.0;
+        if (codes_after)
+            memset(codes_after, 0, (size_t)(rounds + 1) * (size_t)len);
+        if (init_margin)
+            for (i = 0; i < len; ++i) init_margin[i] = INFINITY;
+        if (dplus)
+            for (i = 0; i < rounds * len; ++i) dplus[i] = dminus[i] = -INFINITY;
         return 0;
     }
     const double norm = sqrt(nrm2);
@@ -94,6 +103,7 @@ int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
         if (cmax >= 1) {
             double m = fabs(t - kb) * delta / norm;
             if (m < *min_init_margin) *min_init_margin = m;
+            if (init_margin) init_margin[i] = m;
         }
         /* quantized value o_bar[i] = Delta (c + 0.5) - vmax */
         x[i] = delta * ((double)ci + 0.5) - vmax;
@@ -101,12 +111,30 @@ int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
         sq += x[i] * x[i];
     }
     *init_cos = objective(dot, sq, norm);
+    if (codes_after)
+        for (i = 0; i < len; ++i) codes_after[i] = (uint8_t)c[i];
 
     /* Algorithm 1: coordinate-descent rounds.  For each coordinate in order,
      * try +Delta and then -Delta; keep a move iff the new value stays inside
      * [-vmax, vmax] and the cosine strictly increases. */
     for (r = 0; r < rounds; ++r) {
         for (i = 0; i < len; ++i) {
+            if (dplus) {
+                /* both moves from the state at the start of this step */
+                const double l0 = objective(dot, sq, norm);
+                for (int s = 0; s < 2; ++s) {
+                    const double step = (s == 0) ? delta : -delta;
+                    const int cn = c[i] + ((s == 0) ? 1 : -1);
+                    double *out = (s == 0) ? dplus : dminus;
+                    if (cn < 0 || cn > cmax) {
+                        out[(size_t)r * len + i] = -INFINITY;
+                        continue;
+                    }
+                    const double xn = x[i] + step;
+                    out[(size_t)r * len + i] =
+                        objective(dot + step * o[i], sq - x[i] * x[i] + xn * xn, norm) - l0;
+                }
+            }
             for (int s = 0; s < 2; ++s) {
                 const double step = (s == 0) ? delta : -delta;
                 const int cn = c[i] + ((s == 0) ? 1 : -1);
@@ -129,6 +157,8 @@ int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
                 }
             }
         }
+        if (codes_after)
+            for (i = 0; i < len; ++i) codes_after[(size_t)(r + 1) * len + i] = (uint8_t)c[i];
     }
     /* Final code c_a from Eq. find_nearest_code applied to o_bar_a; it equals
      * the tracked integer code because o_bar_a sits on interval midpoints. */
@@ -143,6 +173,52 @@ int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
     *cos_out = objective(dot, sq, norm);
     free(x);
     free(c);
+    return total;
+}
+
+/*
+ * Quantize one segment o[0..len) with B bits (1 <= B <= 8) and adjust the
+ * code for `rounds` rounds (Algorithm 1).
+ *
+ * Outputs:
+ *   code[len]          final codes c_a in [0, 2^B - 1]
+ *   *norm_out          |o|
+ *   *cos_out           L(o_bar_a, o), the cosine between the adjusted quantized
+ *                      vector and o (the second stored factor, Sec. 3.1 end)
+ *   accepts[rounds]    number of accepted moves in each round
+ *   *min_trial_margin  min over all in-range trials of |L(x') - L(x)|
+ *   *min_init_margin   min over coordinates of the distance from o[i] to the
+ *                      nearest interior interval boundary of the initial grid,
+ *                      divided by |o| (how far o[i] must move, relative to the
+ *                      segment norm, to change its initial code)
+ *   *init_cos          L(o_bar, o) of the initial (unadjusted) code
+ * Returns the number of accepted moves in total.
+ */
+int saq_oracle_caq_segment(const double *o, int len, int B, int rounds,
+                           uint8_t *code, double *norm_out, double *cos_out,
+                           int *accepts, double *min_trial_margin,
+                           double *min_init_margin, double *init_cos) {
+    return caq_run(o, len, B, rounds, code, norm_out, cos_out, accepts,
+                   min_trial_margin, min_init_margin, init_cos, NULL, NULL,
+                   NULL, NULL);
+}
+
+/*
+ * The same run, recording every decision (see caq_run): codes_after is
+ * (rounds + 1) x len, init_margin len, dplus and dminus rounds x len.  Used
+ * to find where another implementation's codes first leave the oracle's and
+ * how close that decision was.  Returns the number of accepted moves.
+ */
+int saq_oracle_caq_trace(const double *o, int len, int B, int rounds,
+                         uint8_t *codes_after, double *init_margin,
+                         double *dplus, double *dminus) {
+    uint8_t *code = (uint8_t *)malloc((size_t)(len > 0 ? len : 1));
+    int *acc = (int *)malloc(sizeof(int) * (size_t)(rounds > 0 ? rounds : 1));
+    double nrm, cs, mt, mi, ic;
+    const int total = caq_run(o, len, B, rounds, code, &nrm, &cs, acc, &mt, &mi,
+                              &ic, codes_after, init_margin, dplus, dminus);
+    free(code);
+    free(acc);
     return total;
 }
 

@@ -56,6 +56,9 @@ def _c():
             ctypes.c_double, ip, ip, ip, ip, dp, dp, i64p]
         lib.saq_oracle_plan.restype = ctypes.c_int
         lib.saq_oracle_max_threads.restype = ctypes.c_int
+        lib.saq_oracle_caq_trace.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             u8p, dp, dp, dp]
+        lib.saq_oracle_caq_trace.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -260,6 +263,75 @@ def caq_segment(o: np.ndarray, B: int, rounds: int):
                                 ctypes.byref(mt), ctypes.byref(mi),
                                 ctypes.byref(ic))
     return code, nrm.value, cs.value, acc[:rounds].copy(), mt.value, mi.value, ic.value
+
+
+@dataclass
+class Trace:
+    """Every decision of one run of Algorithm 1 on one segment."""
+    codes_after: np.ndarray   # (rounds + 1, len) uint8: initial codes, then after each round
+    init_margin: np.ndarray   # (len,) distance of o_i to its nearest interior boundary / |o|
+    dplus: np.ndarray         # (rounds, len) L(x + Delta e_i) - L(x) when round r reaches i
+    dminus: np.ndarray        # (rounds, len) L(x - Delta e_i) - L(x) from the same state
+
+    def gap(self, r: int, i: int, a: int, b: int) -> float:
+        """|L(c + a) - L(c + b)| for moves a, b in {-1, 0, +1} of coordinate i
+        from the state at which round r (1-based) reaches it: how far apart
+        in the objective two outcomes of that decision are (inf if a move
+        leaves the code range)."""
+        d = {0: 0.0, 1: self.dplus[r - 1, i], -1: self.dminus[r - 1, i]}
+        if not (np.isfinite(d[a]) and np.isfinite(d[b])):
+            return math.inf
+        return abs(d[a] - d[b])
+
+
+def caq_trace(o: np.ndarray, B: int, rounds: int) -> Trace:
+    """Replay CAQ on one segment (Sec. 3.1, Algorithm 1) and record every
+    decision: the codes after each round and, for each (round, coordinate),
+    the objective change of either move from the state the scan is in when
+    it reaches that coordinate.  The run itself is the one caq_segment
+    performs; the record only observes it."""
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    n = o.shape[0]
+    ca = np.zeros((rounds + 1, n), dtype=np.uint8)
+    im = np.zeros(n)
+    dp_ = np.zeros((max(rounds, 1), n))
+    dm = np.zeros((max(rounds, 1), n))
+    _c().saq_oracle_caq_trace(_ptr(o, ctypes.c_double), n, B, rounds,
+                              _ptr(ca, ctypes.c_uint8), _ptr(im, ctypes.c_double),
+                              _ptr(dp_, ctypes.c_double), _ptr(dm, ctypes.c_double))
+    return Trace(ca, im, dp_[:rounds], dm[:rounds])
+
+
+def first_divergence(o: np.ndarray, B: int, rounds: int, other_after) -> Tuple[int, int, float]:
+    """Where another run of Algorithm 1 on segment o first leaves the
+    oracle's, and how close that decision was.
+
+    other_after[r] holds the other run's codes of this segment after r rounds
+    (r = 0: initial codes).  Returns (r, i, margin) for the first round r and,
+    within it, the first coordinate i whose code differs.  Up to that point
+    both runs made the same decisions, so both arrive at coordinate i in the
+    same state, and the margin is the oracle's objective gap between the two
+    outcomes there: for r = 0 the distance of o_i to the nearest interval
+    boundary of the initial grid over |o|; for r >= 1, |L(c + a) - L(c + b)|
+    for the oracle's move a and the other run's move b (inf if b is not a
+    single step inside the code range).  (-1, -1, 0.0) if the runs agree."""
+    tr = caq_trace(o, B, rounds)
+    for r in range(rounds + 1):
+        mine = tr.codes_after[r]
+        theirs = np.asarray(other_after[r]).astype(np.int64)
+        diff = np.nonzero(mine.astype(np.int64) != theirs)[0]
+        if diff.size == 0:
+            continue
+        i = int(diff[0])
+        if r == 0:
+            return 0, i, float(tr.init_margin[i])
+        prev = int(tr.codes_after[r - 1, i])
+        a = int(mine[i]) - prev
+        b = int(theirs[i]) - prev
+        if b not in (-1, 0, 1):
+            return r, i, math.inf
+        return r, i, float(tr.gap(r, i, a, b))
+    return -1, -1, 0.0
 
 
 def encode_projected(O: np.ndarray, norms2: np.ndarray, model: Model,

@@ -475,6 +475,122 @@ def test_progressive_prefix_is_a_valid_estimator():
     assert p1 < 0.5
 
 
+def test_progressive_prefix_worked_example():
+    """Sec. 3.2: the b-bit prefix floor(c / 2^(B-b)) with Delta' = Delta 2^(B-b)
+    and the stored factors reused, against values worked by hand
+    (tests/golden/prefix_worked_example.txt).  A wrong grid offset (2^B - 1
+    instead of 2^b - 1), a prefix taken from the low bits, or a norm of the
+    full code in place of the prefix's fails it."""
+    g = golden("prefix_worked_example.txt")
+    m = O.Model(d=4, mean=np.zeros(4), W=np.eye(4), plan=[(0, 4, int(g["bits"][0]))])
+    codes = np.array([[int(v) for v in g["codes"]]], dtype=np.uint8)
+    factors = np.array([[float(v) for v in g["factors"]]])
+    q = np.array([[float(v) for v in g["query"]]])
+    for b in (3, 2, 1):
+        want = float(g["d2_b%d" % b][0])
+        got = O.estimate(m, codes, factors, q, prefix_bits=b)[0, 0]
+        assert got == pytest.approx(want, rel=1e-14), b
+    # prefix_bits >= B (and 0) is the full code
+    assert O.estimate(m, codes, factors, q, prefix_bits=5)[0, 0] == pytest.approx(
+        float(g["d2_b3"][0]), rel=1e-14)
+
+
+# ------------------------------------------------- decision trace of Alg. 1
+def _state_before(tr, r, i):
+    """Codes of the state at which round r (1-based) reaches coordinate i:
+    coordinates before i already carry round r's values."""
+    c = tr.codes_after[r - 1].astype(np.int64).copy()
+    c[:i] = tr.codes_after[r, :i]
+    return c
+
+
+@pytest.mark.parametrize("B", [2, 3, 5])
+def test_trace_gaps_are_cosine_differences_from_scratch(B):
+    """Each recorded gap equals the change of the cosine of Eq. adj-obj,
+    recomputed from scratch (codeword Delta (c + 0.5) - v_max, no running
+    state), of moving coordinate i by +-1 from the state the scan is in when
+    it reaches i; moves out of [0, 2^B - 1] are -inf."""
+    rng = np.random.default_rng(40 + B)
+    o = rng.standard_normal(23) * np.linspace(1.5, 0.3, 23)
+    rounds = 4
+    tr = O.caq_trace(o, B, rounds)
+    v = np.max(np.abs(o))
+    delta = 2 * v / 2 ** B
+    cmax = 2 ** B - 1
+    for r in range(1, rounds + 1):
+        for i in range(len(o)):
+            c = _state_before(tr, r, i)
+            base = cos_explicit(delta * (c + 0.5) - v, o)
+            for s, rec in ((1, tr.dplus), (-1, tr.dminus)):
+                if not 0 <= c[i] + s <= cmax:
+                    assert rec[r - 1, i] == -np.inf
+                    continue
+                cn = c.copy()
+                cn[i] += s
+                want = cos_explicit(delta * (cn + 0.5) - v, o) - base
+                assert rec[r - 1, i] == pytest.approx(want, abs=1e-13)
+
+
+@pytest.mark.parametrize("B", [2, 4, 6])
+def test_trace_decisions_follow_algorithm_1(B):
+    """The recorded codes move exactly as Algorithm 1 decides from the
+    recorded gaps (+Delta first, kept iff the cosine strictly rises; -Delta
+    only if +Delta was not kept), the last row is the plain run's code and
+    every row r equals a plain run of r rounds; the per-coordinate initial
+    margins are the distances to the nearest interior interval boundary
+    (brute force over the 2^B - 1 boundaries of Eq. find_nearest_code)."""
+    rng = np.random.default_rng(60 + B)
+    o = rng.standard_normal(57) * np.linspace(2.0, 0.2, 57)
+    rounds = 5
+    tr = O.caq_trace(o, B, rounds)
+    for r in range(rounds + 1):
+        assert np.array_equal(tr.codes_after[r], O.caq_segment(o, B, r)[0])
+    moves = tr.codes_after[1:].astype(int) - tr.codes_after[:-1].astype(int)
+    want = np.where(tr.dplus > 0, 1, np.where(tr.dminus > 0, -1, 0))
+    assert np.array_equal(moves, want)
+    v = np.max(np.abs(o))
+    delta = 2 * v / 2 ** B
+    bounds = -v + delta * np.arange(1, 2 ** B)
+    brute = np.min(np.abs(o[:, None] - bounds[None, :]), axis=1) / np.linalg.norm(o)
+    assert np.allclose(tr.init_margin, brute, rtol=1e-12, atol=1e-15)
+    assert tr.gap(1, 0, 0, 0) == 0.0
+    assert tr.gap(1, 0, 1, 0) == pytest.approx(abs(tr.dplus[0, 0]))
+
+
+def test_first_divergence_localises_a_planted_change():
+    """first_divergence finds the first round and coordinate at which another
+    run's codes leave the oracle's and reports the oracle's gap between the
+    two outcomes there: a copy of the oracle's own run has none; a run that
+    flips one decision of round 2 is found at that decision with the gap
+    |dplus| (or |dminus|, or their difference); a changed initial code is
+    found at round 0 with that coordinate's boundary distance; a jump of two
+    code steps has an infinite gap."""
+    rng = np.random.default_rng(77)
+    o = rng.standard_normal(64) * np.linspace(2.0, 0.5, 64)
+    B, R = 4, 6
+    tr = O.caq_trace(o, B, R)
+    assert O.first_divergence(o, B, R, tr.codes_after) == (-1, -1, 0.0)
+    for i in (3, 17, 40):
+        alt = tr.codes_after.astype(int).copy()
+        prev = alt[1, i]
+        a = alt[2, i] - prev
+        b = 0 if a != 0 else (1 if prev < 2 ** B - 1 else -1)
+        alt[2:, i] = prev + b            # the other run decides differently here
+        alt[2:, i + 1:] += 0             # later coordinates unchanged
+        r, j, m = O.first_divergence(o, B, R, alt)
+        assert (r, j) == (2, i)
+        d = {0: 0.0, 1: tr.dplus[1, i], -1: tr.dminus[1, i]}
+        assert m == pytest.approx(abs(d[a] - d[b]), rel=1e-15)
+    alt = tr.codes_after.astype(int).copy()
+    alt[:, 9] = np.clip(alt[:, 9] + 1, 0, 2 ** B - 1) if alt[0, 9] < 2 ** B - 1 else alt[:, 9] - 1
+    r, j, m = O.first_divergence(o, B, R, alt)
+    assert (r, j) == (0, 9) and m == pytest.approx(tr.init_margin[9])
+    alt = tr.codes_after.astype(int).copy()
+    k = int(np.argmax((alt[0] >= 2) & (alt[0] <= 2 ** B - 3)))
+    alt[1:, k] = alt[0, k] + 2
+    assert O.first_divergence(o, B, R, alt)[2] == math.inf
+
+
 # ---------------------------------------------------- multi-stage estimation
 def test_segment_sigma_is_the_variance_of_the_segment_inner_product():
     """Sec. 4.3: sigma_Seg^2 = sum_{i in Seg} q[i]^2 sigma_i^2 is the
