@@ -35,10 +35,9 @@ UNIT = "vectors/s"
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per row of one
-# launch of each encode kernel, from `ncu --set full` captures of the 65,536-row
-# case of the default workload (one launch each; profiles/k_proj_tc_split_n65536.md,
-# profiles/k_caq1_n65536.md).  Both kernels stream their rows, so a launch's
-# traffic is proportional to its rows.  A figure is reported only while the
+# launch of each encode kernel, from ncu captures of one launch each on the
+# 65,536-row case of the default workload.  Both kernels stream their rows, so
+# a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
     "projection": {"src": "k_tc.cu", "sha1": "f9ef820d11a2cbfdcee55f35b0ae803b2761020a",
@@ -246,6 +245,47 @@ def cpu_baseline_one_core(mo, X, rounds):
     return {"value": X.shape[0] / dt, "unit": UNIT, "cores": 1, "omp_threads": int(threads),
             "sample": "%d rows of the workload, one pinned CPU, one OpenMP and one BLAS thread, "
                       "%.1f s" % (X.shape[0], dt)}
+
+
+def form_accuracy(m_forms, mo, enc, X_dev, rows=2000, nq=100, alpha=0.8):
+    """Part of the CPU-baseline leg: the error of each projection form
+    against the oracle's FP64 encode of the first `rows` rows of the sample
+    that leg timed.  The library encodes the same rows with the oracle's
+    model (imported, so rotations and plan are the same) in each form;
+    reported: code agreement, mean quantization error eps against the
+    oracle's, the largest per-vector |eps difference|, and the mean relative
+    error of the library's distance estimates for `nq` queries (exact
+    distances in FP64 on the GPU) beside that of the oracle's codes run
+    through the same estimator."""
+    import oracle as O
+    ns = min(rows, enc.codes.shape[0])
+    Xs = X_dev[:ns].contiguous()
+    Q = synth.queries(nq, X_dev.shape[1], alpha, device=X_dev.device)
+    X64, Q64 = Xs.double(), Q.double()
+    exact = ((Q64 * Q64).sum(1)[:, None] + (X64 * X64).sum(1)[None, :] - 2.0 * Q64 @ X64.T)
+
+    def rel_err(m, codes, factors):
+        est = m.estimate_dist(codes, factors, Q).double()
+        return float(((est - exact).abs() / exact.clamp_min(1e-300)).mean())
+
+    eps_o = O.quant_error(enc.factors[:ns], mo)
+    codes_o = torch.from_numpy(O.pack(enc.codes[:ns], mo)).to(X_dev.device)
+    fac_o = torch.from_numpy(enc.factors[:ns].astype(np.float32)).to(X_dev.device)
+    out = {}
+    for prec in m_forms:
+        m = P.saq_model_create(mo.d, mo.mean, mo.W, mo.plan, mo.sig2, rounds=6, precision=prec)
+        c, f = m.encode(Xs)
+        cu = O.unpack(c.cpu().numpy(), mo)
+        eps = O.quant_error(f.cpu().numpy().astype(np.float64), mo)
+        out[prec] = {"code_agreement": float((cu == enc.codes[:ns]).mean()),
+                     "mean_eps": float(eps.mean()), "oracle_mean_eps": float(eps_o.mean()),
+                     "max_abs_eps_diff": float(np.abs(eps - eps_o).max()),
+                     "mean_rel_dist_err": rel_err(m, c, f),
+                     "oracle_codes_mean_rel_dist_err": rel_err(m, codes_o, fac_o),
+                     "sample": "%d rows x %d queries of the workload, oracle model imported"
+                               % (ns, nq)}
+        del m
+    return out
 
 
 # Algorithmic lane operations of quantize / adjust / pack (Eq. find_nearest_code,
@@ -508,6 +548,15 @@ def run_ours(args):
     alu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, mo, enc = cpu_baseline(w, X)
+        # the same leg: each projection form's error against the oracle
+        try:
+            acc = form_accuracy(["fp32"] + list(forms), mo, enc, X, alpha=w["alpha"])
+            for prec, a in acc.items():
+                if prec in forms:
+                    forms[prec]["accuracy_vs_oracle"] = a
+            cpu["fp32_accuracy_vs_oracle"] = acc.get("fp32")
+        except Exception as e:  # noqa: BLE001
+            cpu["accuracy_error"] = "%s: %s" % (type(e).__name__, str(e)[:200])
         if mo.plan == plan:
             ops, steps = alu_ops_per_vector(enc, mo, w["rounds"])
             # the step's own instruction ceiling at the quantize kernel's
@@ -530,16 +579,6 @@ def run_ours(args):
     if rank == 0:
         cfg = workload_desc(w, args.workload, args.precision, plan, m.code_bytes)
         cfg["parallelism"] = "replicas x%d (independent batches)" % world
-        # the quantize kernel is bound by the issue of its step chain, not by
-        # HBM: with the ALU term counted, that is its roofline (the HBM view
-        # of the same launches stays beside it)
-        if dom == "quantize_adjust_pack" and alu is not None:
-            roof = dict(alu)
-            roof["traffic"] = caq_roof["traffic"]
-            roof["hbm_view"] = {k: caq_roof[k] for k in ("achieved", "peak", "unit", "frac",
-                                                          "algorithmic_bytes_per_launch",
-                                                          "dram_traffic_gbs", "dram_traffic_frac")
-                                if k in caq_roof}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": max(3, args.warmup),
                "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,

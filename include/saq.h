@@ -43,7 +43,10 @@ typedef enum {
     SAQ_ERR_CUDA = 2,        /* a CUDA runtime / library call failed        */
     SAQ_ERR_OOM = 3,         /* device or host allocation failed            */
     SAQ_ERR_TIMEOUT = 4,     /* a bounded device wait gave up               */
-    SAQ_ERR_UNSUPPORTED = 5  /* valid request the build does not support    */
+    SAQ_ERR_UNSUPPORTED = 5, /* valid request the build does not support    */
+    SAQ_ERR_RANGE = 6        /* an input row is not finite or lies outside
+                                the range of the projection's operand format;
+                                the outputs of that call are invalid        */
 } saq_status;
 
 /* Arithmetic of the projection GEMM (Sec. 5.1 combined matrix).  Quantization
@@ -219,7 +222,10 @@ saq_status saq_quantize_projected_ex(const saq_model *m, const float *O_dev,
  * are as for saq_encode.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any
- * stream capture.  Every call shares the one array, so calls whose work
+ * stream capture.  The looked-up address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys and
+ * recreates the device's primary context) the kept address is stale, so
+ * this entry point must not be used on that device again.  Every call shares the one array, so calls whose work
  * overlaps on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  The array keeps the last call's contents:
  * each call clears the per-segment maxima (which must start at zero) on its
@@ -272,9 +278,30 @@ saq_status saq_plan_search(const double *sig2, int32_t d, int32_t g, int64_t quo
 int32_t saq_model_uses_tensor_cores(const saq_model *m);
 
 /* Synchronise `stream`, then report whether a bounded device wait inside the
- * model's kernels gave up since the last check (SAQ_ERR_TIMEOUT; the flag is
- * cleared).  Failure detection for the asynchronous entry points. */
+ * model's kernels gave up (SAQ_ERR_TIMEOUT) or an input row was out of range
+ * (SAQ_ERR_RANGE) since the last check; the flag is cleared.  Failure
+ * detection for the asynchronous entry points (saq_encode_host, which is
+ * synchronous, reports both itself).  The range check of the tensor-core
+ * projection is on the scaled, centred squared row norm |(x - c) s|^2, s the
+ * power of two that maps the fitted per-coordinate rms to 8 (FP32 split):
+ * it fires at 65504^2, the square of FP16's largest value, i.e. when a row's
+ * |x - c| reaches about 8,000 times the fitted rms (a coordinate could
+ * overflow the split there); the BF16 and FP8 forms flag non-finite rows
+ * only (E4M3 saturates at 448, see SAQ_PREC_FP8). */
 saq_status saq_check_device(const saq_model *m, void *stream);
+
+/* Failure detection (no counterpart in the paper): the bound, in
+ * nanoseconds, of every pipeline wait inside the tensor-core projection
+ * (TMA producer, MMA issuer and converters waiting on one another) for
+ * launches that start after the call; 0 restores the default of 2 s.  A
+ * wait that reaches its bound raises the device error flag, every role
+ * leaves its loop, the copies and MMAs already in flight are drained (those
+ * drain waits keep the 2 s bound), tensor memory is freed and the kernel
+ * returns; the next saq_check_device (or saq_encode_host itself) returns
+ * SAQ_ERR_TIMEOUT and clears the flag.  Process-wide; meant for tests of
+ * that path (a bound of a few nanoseconds makes the waits run out) and for
+ * hosts that want a tighter watchdog.  Always SAQ_OK. */
+saq_status saq_set_wait_limit(uint64_t ns);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous-batching ingest over several resident collections.

@@ -37,7 +37,7 @@ EXPORTS = [
     "saq_ingest_open", "saq_ingest_submit", "saq_ingest_poll", "saq_ingest_wait",
     "saq_ingest_get_stats", "saq_ingest_close", "saq_project_ex", "saq_quantize_projected_ex",
     "saq_kernel_timing", "saq_kernel_times", "saq_estimate_staged", "saq_model_set_basis",
-    "saq_model_has_basis", "saq_quantize_step_ceiling",
+    "saq_model_has_basis", "saq_quantize_step_ceiling", "saq_set_wait_limit",
 ]
 
 
@@ -111,6 +111,7 @@ def load() -> ctypes.CDLL:
         "saq_kernel_launch_count": (ctypes.c_uint64, []),
         "saq_kernel_timing": (st, [ctypes.c_int]),
         "saq_quantize_step_ceiling": (st, [i32, i32, ctypes.POINTER(ctypes.c_double)]),
+        "saq_set_wait_limit": (st, [ctypes.c_uint64]),
         "saq_estimate_staged": (st, [mp, vp, vp, i64, vp, i64, ctypes.c_float, vp, vp]),
         "saq_model_set_basis": (st, [mp, ctypes.POINTER(ctypes.c_double)]),
         "saq_model_has_basis": (ctypes.c_int32, [mp]),
@@ -404,6 +405,12 @@ def saq_quantize_step_ceiling(warps_per_sm: int = 32, bits: int = 4) -> float:
     out = ctypes.c_double(0.0)
     _check(load().saq_quantize_step_ceiling(int(warps_per_sm), int(bits), ctypes.byref(out)))
     return float(out.value)
+
+
+def saq_set_wait_limit(ns: int) -> None:
+    """Bound (ns) of the projection's pipeline waits for later launches; 0
+    restores the default (2 s)."""
+    _check(load().saq_set_wait_limit(int(ns)))
 
 
 def saq_kernel_timing(enable: bool) -> None:

@@ -44,6 +44,26 @@ struct SegTable {
     Seg s[kMaxSeg];
     int order[kMaxSeg];  // segments by decreasing length: long work starts first
 };
+// One model's rows of a launch: its interleaved projected rows, byte-code
+// scratch, v_max and outputs.
+struct CaqGroup {
+    const float *Oi;
+    int64_t n;
+    int dk, nseg, rounds, nf;
+    uint8_t *cs;
+    const float *vmax;
+    uint8_t *codes;
+    int64_t code_stride;
+    float *factors;
+    SegTable t;
+};
+// A launch over G models: global warp w belongs to the group g with
+// warp_start[g] <= w < warp_start[g + 1] (ngroups <= G).
+template <int G> struct CaqBatch {
+    int ngroups;
+    int64_t warp_start[G + 1];
+    CaqGroup g[G];
+};
 
 // Bit-planes of one lane's segment from its codes (most significant first,
 // 64-bit words); returns |u|^2 of the codes, exactly.
@@ -216,18 +236,16 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t 
     return Si;
 }
 
-// One warp per (kept segment, group of 32 rows); all kept segments of a
-// chunk in one launch.  Four blocks of 256 threads per SM (64 registers):
-// the packing round spills a little, which costs less than the lower
-// occupancy of an uncapped build.
-__global__ void __launch_bounds__(256, 4)
-k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable t, int rounds,
-       uint8_t *__restrict__ cs, const float *__restrict__ vmax_arr,
-       uint8_t *__restrict__ codes, int64_t code_stride, float *__restrict__ factors, int nf) {
+// The work of warp w of one model's launch: one warp per (kept segment,
+// group of 32 rows).
+__device__ __forceinline__ void caq1_warp(int64_t w, const float *__restrict__ Oi, int64_t n,
+                                          int dk, int nseg, const SegTable &t, int rounds,
+                                          uint8_t *__restrict__ cs,
+                                          const float *__restrict__ vmax_arr,
+                                          uint8_t *__restrict__ codes, int64_t code_stride,
+                                          float *__restrict__ factors, int nf) {
     const int lane = threadIdx.x & 31;
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t groups = (n + 31) / 32;
-    if (w >= groups * nseg) return;  // uniform per warp
     const int si = t.order[w / groups];
     const Seg sg = t.s[si];
     const int64_t g = w % groups;
@@ -319,6 +337,32 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
     }
 }
 
+// All kept segments of a chunk in one launch.  Four blocks of 256 threads
+// per SM (64 registers): the packing round spills a little, which costs less
+// than the lower occupancy of an uncapped build.
+__global__ void __launch_bounds__(256, 4)
+k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable t, int rounds,
+       uint8_t *__restrict__ cs, const float *__restrict__ vmax_arr,
+       uint8_t *__restrict__ codes, int64_t code_stride, float *__restrict__ factors, int nf) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (n + 31) / 32 * nseg) return;  // uniform per warp
+    caq1_warp(w, Oi, n, dk, nseg, t, rounds, cs, vmax_arr, codes, code_stride, factors, nf);
+}
+
+// The rows of up to kMaxGroups models (a batch of several collections) in
+// one launch: global warp w belongs to the group g with warp_start[g] <= w <
+// warp_start[g + 1].
+__global__ void __launch_bounds__(256, 4)
+k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch) {
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int gi = 0;
+    while (gi + 1 < batch.ngroups && wg >= batch.warp_start[gi + 1]) ++gi;
+    if (wg >= batch.warp_start[batch.ngroups]) return;  // uniform per warp
+    const CaqGroup &P = batch.g[gi];
+    caq1_warp(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds, P.cs, P.vmax,
+              P.codes, P.code_stride, P.factors, P.nf);
+}
+
 // The instruction ceiling of the adjustment: caq_step on coordinates held in
 // registers (no loads or stores), kU per lane, a sign flip per step keeping
 // moves happening; one block of 256 threads per 8 warps of occupancy.
@@ -387,12 +431,13 @@ __global__ void k_interleave(const float *__restrict__ O, int64_t ldo, int64_t n
 
 }  // namespace
 
-saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
-                       const float *vmax, uint8_t *codes, float *factors, cudaStream_t s) {
+namespace {
+
+saq_status make_group(const CaqJob &j, CaqGroup *g) {
+    const saq_model *m = j.m;
     const int nk = (int)m->kept.size();
-    if (n <= 0 || nk == 0) return SAQ_OK;
     if (nk > kMaxSeg) return set_error(SAQ_ERR_UNSUPPORTED, "more than %d kept segments", kMaxSeg);
-    SegTable t;
+    SegTable &t = g->t;
     for (int i = 0; i < nk; ++i) {
         const KeptSeg &k = m->kept[(size_t)i];
         if (k.bits < 1 || k.bits > 8)
@@ -401,12 +446,59 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
         t.order[i] = i;
     }
     std::stable_sort(t.order, t.order + nk, [&](int a, int b) { return t.s[a].len > t.s[b].len; });
-    const int64_t warps = (n + 31) / 32 * nk;
+    g->Oi = j.Oi;
+    g->n = j.n;
+    g->dk = m->dk;
+    g->nseg = nk;
+    g->rounds = m->rounds;
+    g->nf = m->nf;
+    g->cs = j.cs;
+    g->vmax = j.vmax;
+    g->codes = j.codes;
+    g->code_stride = (int64_t)m->code_bytes;
+    g->factors = j.factors;
+    return SAQ_OK;
+}
+
+}  // namespace
+
+saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
+                       const float *vmax, uint8_t *codes, float *factors, cudaStream_t s) {
+    if (n <= 0 || m->kept.empty()) return SAQ_OK;
+    CaqGroup g;
+    saq_status st = make_group(CaqJob{m, Oi, n, cs, vmax, codes, factors}, &g);
+    if (st != SAQ_OK) return st;
+    const int64_t warps = (n + 31) / 32 * g.nseg;
     const int64_t blocks = (warps + 7) / 8;
     {
         LaunchTimer lt_(kKindQuantize, s);
-        k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, m->dk, nk, t, m->rounds, cs, vmax, codes,
-                                                (int64_t)m->code_bytes, factors, m->nf);
+        k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, g.dk, g.nseg, g.t, g.rounds, cs, vmax,
+                                                codes, g.code_stride, factors, g.nf);
+    }
+    note_launches();
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return SAQ_OK;
+}
+
+saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s) {
+    if (njobs < 1 || njobs > kMaxGroups)
+        return set_error(SAQ_ERR_INVALID, "1..%d models per grouped launch", kMaxGroups);
+    CaqBatch<kMaxGroups> b;
+    b.ngroups = 0;
+    b.warp_start[0] = 0;
+    for (int i = 0; i < njobs; ++i) {
+        if (jobs[i].n <= 0 || jobs[i].m->kept.empty()) continue;
+        saq_status st = make_group(jobs[i], &b.g[b.ngroups]);
+        if (st != SAQ_OK) return st;
+        b.warp_start[b.ngroups + 1] =
+            b.warp_start[b.ngroups] + (jobs[i].n + 31) / 32 * (int64_t)b.g[b.ngroups].nseg;
+        ++b.ngroups;
+    }
+    if (b.ngroups == 0) return SAQ_OK;
+    const int64_t blocks = (b.warp_start[b.ngroups] + 7) / 8;
+    {
+        LaunchTimer lt_(kKindQuantize, s);
+        k_caq1_grouped<<<(unsigned)blocks, 256, 0, s>>>(b);
     }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());

@@ -50,8 +50,10 @@
 #include <cuda_fp8.h>
 
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "saq_internal.h"
@@ -67,6 +69,9 @@ constexpr int kNPMax = 256;         // output columns per tile at most (UMMA N)
 constexpr int kPrefetch = 8;        // X boxes are prefetched into L2 this many K blocks ahead
 constexpr int kAcc2 = 256;          // TMEM column of the split mode's correction accumulator
 constexpr int kConvWarps = 8;
+// error word: 1..5 the role whose wait timed out; kErrRange an input row
+// outside the operand format's range (or not finite)
+constexpr int kErrRange = 16;
 constexpr int kThreads = 64 + 32 * kConvWarps;
 constexpr uint32_t kXBox = 16384;   // 128 rows x 128 bytes of staged FP32
 constexpr uint32_t kATile = 8192;   // 128 rows x 64 bytes
@@ -151,18 +156,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Bound of the drain waits (in-flight copies and MMAs at exit), which always
+// end; the role waits of the pipeline take their bound from the launch
+// (kWaitNs unless saq_set_wait_limit changed it).
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 // Bounded wait for the phase of `parity` to complete.  Returns false on a
-// timeout (after raising the flags) or when another role already aborted.
+// timeout after `limit_ns` (after raising the flags) or when another role
+// already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int *err, int code) {
+                                          int *err, int code, uint64_t limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
+    // a bound below 10 us is checked on every poll, so that a wait longer
+    // than it gives up however few polls it took
+    const uint32_t every = limit_ns < 10000ull ? 0u : 255u;
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 0u) {
+        if ((it & every) == 0u) {
             if (*abort_flag) return false;
-            if (globaltimer() - t0 > kWaitNs) {
+            if (globaltimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicCAS(err, 0, code);
                 return false;
@@ -317,14 +329,16 @@ __device__ __forceinline__ uint32_t swz64(int r, int c) {
     return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
+// The work of one CTA: row tile `tile`, column pass `pass` of one model
+// (tmx: the tensor map of its X rows, in parameter space).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
-k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ wt0,
-          const uint8_t *__restrict__ wt1, int64_t n, int dk, int npass, int np, int nkb,
-          const float *__restrict__ mcs_g, float x_scale, const float *__restrict__ col_scale,
-          float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms,
-          int64_t nstride, float *__restrict__ vmax, const SegCols segc,
-          int *__restrict__ err) {
+__device__ __forceinline__ void proj_tile(
+    const CUtensorMap *tmxp, int64_t tile, int pass, const uint8_t *__restrict__ wt0,
+    const uint8_t *__restrict__ wt1, int64_t n, int dk, int npass, int np, int nkb,
+    const float *__restrict__ mcs_g, float x_scale, const float *__restrict__ col_scale,
+    float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms, int64_t nstride,
+    float *__restrict__ vmax, const SegCols &segc, int *__restrict__ err, uint64_t wait_ns,
+    float norm_limit) {
     using C = Cfg<MODE>;
     constexpr uint32_t SB = stage_bytes<MODE>();
     extern __shared__ uint8_t smem_raw[];
@@ -339,8 +353,6 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
     float *mcs = (float *)(smem + C::STAGES * SB + kBarArea + 512);       // nkb * BK floats
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tile = blockIdx.x / npass;
-    const int pass = (int)(blockIdx.x % npass);
     const int64_t row0 = tile * kBM;
     const int col0 = pass * np;
 
@@ -369,23 +381,23 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
 
     if (warp == 0) {
         if (lane == 0) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmx) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmxp) : "memory");
             const uint32_t tx = (uint32_t)C::XBOX * kXBox + (uint32_t)C::NB * (uint32_t)np * 64u;
             // X boxes kPrefetch K blocks ahead are pulled into L2, so that the
             // stage loads wait on L2 rather than on HBM
             for (int kb = C::STAGES; kb < kPrefetch && kb < nkb; ++kb)
 #pragma unroll
-                for (int b = 0; b < C::XBOX; ++b) tma_prefetch_2d(&tmx, kb * C::BK + b * 32, (int)row0);
+                for (int b = 0; b < C::XBOX; ++b) tma_prefetch_2d(tmxp, kb * C::BK + b * 32, (int)row0);
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % C::STAGES;
                 const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 1)) break;
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 1, wait_ns)) break;
                 uint8_t *st = smem + s * SB;
                 mbar_expect_tx(&full[s], tx);
 #pragma unroll
                 for (int b = 0; b < C::XBOX; ++b)
-                    tma_load_2d(st + b * kXBox, &tmx, kb * C::BK + b * 32, (int)row0, &full[s]);
+                    tma_load_2d(st + b * kXBox, tmxp, kb * C::BK + b * 32, (int)row0, &full[s]);
                 uint8_t *bs = st + b_offset<MODE>();
                 const int64_t wo = ((int64_t)pass * nkb + kb) * np * 64;
                 bulk_load(bs, wt0 + wo, (uint32_t)np * 64u, &full[s]);
@@ -393,7 +405,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                 if (kb + kPrefetch < nkb)
 #pragma unroll
                     for (int b = 0; b < C::XBOX; ++b)
-                        tma_prefetch_2d(&tmx, (kb + kPrefetch) * C::BK + b * 32, (int)row0);
+                        tma_prefetch_2d(tmxp, (kb + kPrefetch) * C::BK + b * 32, (int)row0);
                 issued = kb + 1;
             }
             // drain: the last loads of each stage must land before the CTA exits
@@ -411,7 +423,7 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % C::STAGES;
                 const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-                if (!mbar_wait(&conv[s], ph, abort_flag, err, 2)) break;
+                if (!mbar_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + s * SB);
                 const uint64_t a0 = umma_desc(st + a_offset<MODE>());
@@ -457,8 +469,8 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
             // wait until the MMAs of block kb - STAGES are done (the stage's
             // barriers are then one phase behind this block at most).
             if (lane == 0)
-                got = (kb < C::STAGES || mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 5)) &&
-                              mbar_wait(&full[s], ph, abort_flag, err, 3)
+                got = (kb < C::STAGES || mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 5, wait_ns)) &&
+                              mbar_wait(&full[s], ph, abort_flag, err, 3, wait_ns)
                           ? 1
                           : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
@@ -546,11 +558,18 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
         // |x - c|^2 of the row: the two groups' partial sums meet in shared memory
         if (h == 1) nrm_half[r] = nrm;
         named_sync(1, 32 * kConvWarps);
-        if (h == 0 && pass == 0 && row_ok && norms && ok)
-            norms[(row0 + r) * nstride] = (nrm + nrm_half[r]) / (x_scale * x_scale);
+        if (h == 0 && pass == 0 && row_ok && ok) {
+            const float tot = nrm + nrm_half[r];
+            if (norms) norms[(row0 + r) * nstride] = tot / (x_scale * x_scale);
+            // |y|^2 >= max_k y_k^2: a row whose scaled, centred squared norm
+            // reaches norm_limit may hold a value the operand format cannot
+            // represent (the FP16 split overflows at 65504); a non-finite
+            // row fails the test too
+            if (!(tot < norm_limit)) atomicCAS(err, 0, kErrRange);
+        }
         // ---- epilogue: accumulator row r, columns [h * np/2, (h+1) * np/2)
         int ready = 0;
-        if (ok && lane == 0) ready = mbar_wait(accf, 0, abort_flag, err, 4) ? 1 : 0;
+        if (ok && lane == 0) ready = mbar_wait(accf, 0, abort_flag, err, 4, wait_ns) ? 1 : 0;
         ready = __shfl_sync(0xffffffffu, ready, 0);
         if (ready) {
             tc_fence_after();
@@ -648,6 +667,54 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
     }
 }
 
+// One model's rows: CTA b covers row tile b / npass, column pass b % npass.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ wt0,
+          const uint8_t *__restrict__ wt1, int64_t n, int dk, int npass, int np, int nkb,
+          const float *__restrict__ mcs_g, float x_scale, const float *__restrict__ col_scale,
+          float *__restrict__ O, int64_t ldo, int il, float *__restrict__ norms,
+          int64_t nstride, float *__restrict__ vmax, const SegCols segc,
+          int *__restrict__ err, uint64_t wait_ns, float norm_limit) {
+    proj_tile<MODE>(&tmx, blockIdx.x / npass, (int)(blockIdx.x % npass), wt0, wt1, n, dk, npass,
+                    np, nkb, mcs_g, x_scale, col_scale, O, ldo, il, norms, nstride, vmax, segc,
+                    err, wait_ns, norm_limit);
+}
+
+// One model's part of a grouped launch (interleaved output, v_max, norms).
+struct ProjGroup {
+    CUtensorMap tmx;
+    const uint8_t *wt0, *wt1;
+    const float *mcs_g, *col_scale;
+    float *O, *norms, *vmax;
+    int *err;
+    int64_t n, nstride;
+    int dk, npass, np, nkb;
+    float x_scale, norm_limit;
+    SegCols segc;
+};
+// Rows of up to kMaxGroups models of one precision in one launch (a batch of
+// several collections): CTA b belongs to the group g with block_start[g] <=
+// b < block_start[g + 1].
+struct ProjBatch {
+    int ngroups;
+    uint64_t wait_ns;
+    int64_t block_start[kMaxGroups + 1];
+    ProjGroup g[kMaxGroups];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_proj_tc_grouped(const __grid_constant__ ProjBatch batch) {
+    const int64_t b = blockIdx.x;
+    int gi = 0;
+    while (gi + 1 < batch.ngroups && b >= batch.block_start[gi + 1]) ++gi;
+    const ProjGroup &P = batch.g[gi];
+    const int64_t lb = b - batch.block_start[gi];
+    proj_tile<MODE>(&P.tmx, lb / P.npass, (int)(lb % P.npass), P.wt0, P.wt1, P.n, P.dk, P.npass,
+                    P.np, P.nkb, P.mcs_g, P.x_scale, P.col_scale, P.O, P.dk, 1, P.norms, P.nstride,
+                    P.vmax, P.segc, P.err, batch.wait_ns, P.norm_limit);
+}
+
 // ------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -715,10 +782,16 @@ std::vector<T> tile_operand(const std::vector<T> &w, int dkpad, int dpad, int np
     return t;
 }
 
+// Role-wait bound of the next launches (saq_set_wait_limit).
+std::atomic<uint64_t> g_wait_ns{kWaitNs};
+
 template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, int64_t n,
                                            float *O, int64_t ldo, int layout, float *norms,
-                                           int64_t ns, float *vmax, cudaStream_t s) {
+                                           int64_t ns, float *vmax, int *err, cudaStream_t s) {
     const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
+    // |y|^2 bound of a row (y = (x - c) s): the FP16 split overflows past
+    // 65504; BF16 and E4M3 (saturating) only flag non-finite rows
+    const float norm_limit = MODE == kSplit ? 65504.f * 65504.f : INFINITY;
     CUtensorMap tmx;
     saq_status st = make_map(&tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, X, (uint64_t)m->d,
                              (uint64_t)n, 32, kBM, CU_TENSOR_MAP_SWIZZLE_128B);
@@ -736,7 +809,7 @@ template <int MODE> saq_status launch_mode(const saq_model *m, const float *X, i
             tmx, (const uint8_t *)m->tc.w_hi,
             (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi), n, m->dk, ex->npass, ex->np, nkb, ex->mcs, ex->x_scale,
             m->tc.col_scale, O, ldo, layout == kInterleaved ? 1 : 0, norms, ns, vmax, seg_cols(m),
-            ex->err);
+            err ? err : ex->err, g_wait_ns.load(), norm_limit);
     }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
@@ -863,19 +936,113 @@ SegCols seg_cols(const saq_model *m) {
 
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, float *O,
                              int64_t ldo, int layout, float *norms2, int64_t norms_stride,
-                             float *vmax, cudaStream_t s) {
+                             float *vmax, int *err, cudaStream_t s) {
     if (n <= 0) return SAQ_OK;
     if (((uintptr_t)X & 15u) != 0) return set_error(SAQ_ERR_INVALID, "X not 16-byte aligned");
     if (m->kept.size() > 64) return set_error(SAQ_ERR_UNSUPPORTED, "more than 64 kept segments");
     switch (m->tc.precision) {
         case SAQ_PREC_FP32:
-            return launch_mode<kSplit>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, s);
+            return launch_mode<kSplit>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, err, s);
         case SAQ_PREC_BF16:
-            return launch_mode<kBF16>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, s);
+            return launch_mode<kBF16>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, err, s);
         case SAQ_PREC_FP8:
-            return launch_mode<kFP8>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, s);
+            return launch_mode<kFP8>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, err, s);
     }
     return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
+}
+
+namespace {
+template <int MODE> saq_status launch_grouped_mode(const ProjJob *jobs, int njobs, cudaStream_t s) {
+    ProjBatch b;
+    memset(&b, 0, sizeof(b));
+    b.wait_ns = g_wait_ns.load();
+    b.block_start[0] = 0;
+    int dpad_max = 0;
+    for (int i = 0; i < njobs; ++i) {
+        const ProjJob &j = jobs[i];
+        const saq_model *m = j.m;
+        if (j.n <= 0 || m->dk == 0) continue;
+        const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
+        ProjGroup &g = b.g[b.ngroups];
+        saq_status st = make_map(&g.tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, j.X, (uint64_t)m->d,
+                                 (uint64_t)j.n, 32, kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+        if (st != SAQ_OK) return st;
+        g.wt0 = (const uint8_t *)m->tc.w_hi;
+        g.wt1 = (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi);
+        g.mcs_g = ex->mcs;
+        g.col_scale = m->tc.col_scale;
+        g.O = j.O;
+        g.norms = j.norms;
+        g.vmax = j.vmax;
+        g.err = j.err ? j.err : ex->err;
+        g.n = j.n;
+        g.nstride = j.nstride;
+        g.dk = m->dk;
+        g.npass = ex->npass;
+        g.np = ex->np;
+        g.nkb = m->tc.d_pad / Cfg<MODE>::BK;
+        g.x_scale = ex->x_scale;
+        g.norm_limit = MODE == kSplit ? 65504.f * 65504.f : INFINITY;
+        g.segc = seg_cols(m);
+        dpad_max = std::max(dpad_max, m->tc.d_pad);
+        b.block_start[b.ngroups + 1] = b.block_start[b.ngroups] + (j.n + kBM - 1) / kBM * ex->npass;
+        ++b.ngroups;
+    }
+    if (b.ngroups == 0) return SAQ_OK;
+    const int64_t blocks = b.block_start[b.ngroups];
+    if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
+    const uint32_t sm = smem_bytes<MODE>(dpad_max);
+    SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_grouped<MODE>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
+        LaunchTimer lt_(kKindProject, s);
+        k_proj_tc_grouped<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(b);
+    }
+    note_launches();
+    SAQ_CUDA_CHECK(cudaGetLastError());
+    return SAQ_OK;
+}
+}  // namespace
+
+saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, cudaStream_t s) {
+    if (njobs < 1 || njobs > kMaxGroups)
+        return set_error(SAQ_ERR_INVALID, "1..%d models per grouped launch", kMaxGroups);
+    int prec = -1;
+    for (int i = 0; i < njobs; ++i) {
+        const saq_model *m = jobs[i].m;
+        if (m->dk == 0) continue;
+        if (!tc_supported(m) || m->tc.precision != m->precision || m->precision == SAQ_PREC_FP32_SIMT)
+            return set_error(SAQ_ERR_INVALID, "grouped projection needs tensor-core models");
+        if (((uintptr_t)jobs[i].X & 15u) != 0) return set_error(SAQ_ERR_INVALID, "X not 16-byte aligned");
+        if (m->kept.size() > 64) return set_error(SAQ_ERR_UNSUPPORTED, "more than 64 kept segments");
+        if (prec >= 0 && m->tc.precision != prec)
+            return set_error(SAQ_ERR_INVALID, "grouped projection needs one precision");
+        prec = m->tc.precision;
+    }
+    switch (prec) {
+        case -1: return SAQ_OK;
+        case SAQ_PREC_FP32: return launch_grouped_mode<kSplit>(jobs, njobs, s);
+        case SAQ_PREC_BF16: return launch_grouped_mode<kBF16>(jobs, njobs, s);
+        case SAQ_PREC_FP8: return launch_grouped_mode<kFP8>(jobs, njobs, s);
+    }
+    return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
+}
+
+saq_status tc_error_status(int code) {
+    if (code == 0) return SAQ_OK;
+    if (code == kErrRange)
+        return set_error(SAQ_ERR_RANGE,
+                         "tensor-core projection: an input row is not finite or lies outside the "
+                         "range of the projection's operand format (|x - c| beyond about 8,000 "
+                         "times the fitted per-coordinate rms for the FP32 split); the outputs of "
+                         "that call are invalid");
+    return set_error(SAQ_ERR_TIMEOUT, "tensor-core projection: a device wait timed out (role %d)",
+                     code);
+}
+
+int *tc_error_word(const saq_model *m) {
+    const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
+    return ex ? ex->err : nullptr;
 }
 
 saq_status tc_check_error(const saq_model *m, cudaStream_t s) {
@@ -886,9 +1053,15 @@ saq_status tc_check_error(const saq_model *m, cudaStream_t s) {
     SAQ_CUDA_CHECK(cudaStreamSynchronize(s));
     if (h != 0) {
         cudaMemsetAsync(ex->err, 0, sizeof(int), s);
-        return set_error(SAQ_ERR_TIMEOUT, "tensor-core projection: a device wait timed out (role %d)", h);
+        cudaStreamSynchronize(s);
+        return tc_error_status(h);
     }
     return SAQ_OK;
 }
 
 }  // namespace saq
+
+extern "C" saq_status saq_set_wait_limit(uint64_t ns) {
+    saq::g_wait_ns.store(ns == 0 ? saq::kWaitNs : ns);
+    return SAQ_OK;
+}

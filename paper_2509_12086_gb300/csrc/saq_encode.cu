@@ -29,12 +29,12 @@ int64_t chunk_rows(const saq_model *m, int64_t n, size_t budget) {
     return std::min<int64_t>(r, n);
 }
 
+}  // namespace
+
 bool use_tc(const saq_model *m) {
     return m->precision != SAQ_PREC_FP32_SIMT && m->tc.precision == m->precision &&
            tc_supported(m);
 }
-
-}  // namespace
 
 namespace {
 // Scratch of an encode of up to `rows` rows: interleaved projected rows (FP32),
@@ -69,12 +69,13 @@ size_t encode_scratch_bytes(const saq_model *m, int64_t rows) {
 // Projection of rows [0, n) into O and |x - c|^2 into norms (stride); with
 // the interleaved layout and vmax != NULL also v_max per row and segment.
 saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                        int layout, float *norms, int64_t nstride, float *vmax, cudaStream_t s) {
+                        int layout, float *norms, int64_t nstride, float *vmax, cudaStream_t s,
+                        int *err) {
     if (use_tc(m)) {
         if (vmax && layout == kInterleaved)
             SAQ_CUDA_CHECK(cudaMemsetAsync(vmax, 0, sizeof(float) * (size_t)((n + 31) / 32 * 32) *
                                                        m->kept.size(), s));
-        return launch_project_tc(m, X, n, O, ldo, layout, norms, nstride, vmax, s);
+        return launch_project_tc(m, X, n, O, ldo, layout, norms, nstride, vmax, err, s);
     }
     saq_status st = launch_project_simt(m, X, n, O, ldo, layout, s);
     if (st != SAQ_OK) return st;
@@ -94,12 +95,12 @@ saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, in
 
 // The whole encode of rows [0, n) on stream s with a scratch for `rows` rows.
 saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
-                       float *factors, void *scratch, int64_t rows, cudaStream_t s) {
+                       float *factors, void *scratch, int64_t rows, cudaStream_t s, int *err) {
     for (int64_t r0 = 0; r0 < n; r0 += rows) {
         const int64_t nr = std::min(rows, n - r0);
         const ScratchParts p = scratch_parts(m, scratch, rows);
         saq_status st = project_rows(m, X + r0 * m->d, nr, p.Oi, m->dk, kInterleaved,
-                                     factors + r0 * m->nf, m->nf, p.vmax, s);
+                                     factors + r0 * m->nf, m->nf, p.vmax, s, err);
         if (st != SAQ_OK) return st;
         st = quantize_rows(m, scratch, rows, nr, codes + r0 * (int64_t)m->code_bytes,
                            factors + r0 * m->nf, s);
@@ -332,6 +333,9 @@ saq_status saq_encode_host(const saq_model *m, const float *X_host, int64_t n,
     cudaError_t e = cudaGetLastError();
     if (st != SAQ_OK) return st;
     if (e != cudaSuccess) return set_error(SAQ_ERR_CUDA, "encode_host: %s", cudaGetErrorString(e));
+    // the call is synchronous: a bounded wait that gave up or an input row
+    // out of range is reported here, not left for saq_check_device
+    if (use_tc(m)) return tc_check_error(m, s);
     return SAQ_OK;
 }
 

@@ -272,6 +272,12 @@ saq_status model_finalize(saq_model *m) {
         SAQ_CUDA_CHECK(cudaMemcpy(m->d_W, w.data(), sizeof(float) * w.size(),
                                   cudaMemcpyHostToDevice));
     }
+    // the tensor-core forms take d % 4 == 0 and d <= 6144; another d needs
+    // the CUDA-core projection, chosen explicitly (no silent switch)
+    if (m->precision != SAQ_PREC_FP32_SIMT && m->dk > 0 && !tc_supported(m))
+        return set_error(SAQ_ERR_UNSUPPORTED,
+                         "the tensor-core projection needs d %% 4 == 0 and d <= 6144 (d = %d); "
+                         "use SAQ_PREC_FP32_SIMT for this model", m->d);
     if (m->precision != SAQ_PREC_FP32_SIMT && tc_supported(m)) {
         saq_status st = model_build_tc(m, m->precision, 0);
         if (st != SAQ_OK) return st;
@@ -396,6 +402,7 @@ const char *saq_status_string(saq_status s) {
         case SAQ_ERR_OOM: return "out of memory";
         case SAQ_ERR_TIMEOUT: return "device wait timed out";
         case SAQ_ERR_UNSUPPORTED: return "unsupported";
+        case SAQ_ERR_RANGE: return "input out of range";
     }
     return "unknown status";
 }
@@ -497,11 +504,13 @@ saq_status saq_model_set_precision(saq_model *m, int32_t precision) {
     clear_error();
     if (!m || precision < 0 || precision > 3)
         return set_error(SAQ_ERR_INVALID, "bad model or precision");
-    m->precision = precision;
-    if (precision == SAQ_PREC_FP32_SIMT) return SAQ_OK;
-    if (!tc_supported(m))
+    // checked before anything changes: a refused precision leaves the model as it was
+    if (precision != SAQ_PREC_FP32_SIMT && m->dk > 0 && !tc_supported(m))
         return set_error(SAQ_ERR_UNSUPPORTED,
-                         "tensor-core projection needs d %% 8 == 0 (d = %d)", m->d);
+                         "the tensor-core projection needs d %% 4 == 0 and d <= 6144 (d = %d); "
+                         "use SAQ_PREC_FP32_SIMT for this model", m->d);
+    m->precision = precision;
+    if (precision == SAQ_PREC_FP32_SIMT || m->dk == 0) return SAQ_OK;
     saq_status st = model_build_tc(m, precision, 0);
     if (st != SAQ_OK) return st;
     SAQ_CUDA_CHECK(cudaDeviceSynchronize());

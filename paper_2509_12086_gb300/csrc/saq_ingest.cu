@@ -42,6 +42,8 @@ struct Slot {
     float *X = nullptr, *factors = nullptr;
     void *O = nullptr;
     uint8_t *codes = nullptr;
+    int *err_dev = nullptr;   // the batch's device error word (bounded waits, input range)
+    int *err_host = nullptr;  // its copy, written on the slot stream before the callback
     bool busy = false;
     bool finished = false;  // set by the stream callback
     std::vector<Piece> pieces;
@@ -93,10 +95,15 @@ void reap(saq_ingest *s) {
         // callback itself may still be returning (not-ready is no error)
         const cudaError_t e = cudaStreamQuery(sl.stream);
         const bool failed = e != cudaSuccess && e != cudaErrorNotReady;
+        // a wait of the batch's projection that gave up, or an input row out
+        // of range, fails every request with rows in the batch
+        const saq_status dev_st = *sl.err_host ? saq::tc_error_status(*sl.err_host) : SAQ_OK;
+        *sl.err_host = 0;
         const Clock::time_point now = Clock::now();
         for (const Piece &pc : sl.pieces) {
             Request *r = pc.req;
             if (failed) r->status = SAQ_ERR_CUDA;
+            else if (dev_st != SAQ_OK && r->status == SAQ_OK) r->status = dev_st;
             r->rows_done += pc.nr;
             if (r->rows_done == r->n && !r->done) {
                 r->done = true;
@@ -155,8 +162,13 @@ void dispatch(saq_ingest *s, Slot &sl, int coll) {
             st = SAQ_ERR_CUDA;
     if (st == SAQ_OK) {
         if (m->dk == 0) st = saq::launch_rownorm2(m, sl.X, rows, sl.factors, nf, sl.stream);
-        else st = saq::encode_rows(m, sl.X, rows, sl.codes, sl.factors, sl.O, cap, sl.stream);
+        else st = saq::encode_rows(m, sl.X, rows, sl.codes, sl.factors, sl.O, cap, sl.stream,
+                                   sl.err_dev);
     }
+    if (st == SAQ_OK && (cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int),
+                                         cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+                         cudaMemsetAsync(sl.err_dev, 0, sizeof(int), sl.stream) != cudaSuccess))
+        st = SAQ_ERR_CUDA;
     for (const Piece &pc : sl.pieces) {
         if (cb)
             cudaMemcpyAsync(pc.req->codes + pc.r0 * (int64_t)cb, sl.codes + pc.off * (int64_t)cb,
@@ -209,6 +221,8 @@ void free_slots(saq_ingest *s) {
         cudaFree(sl.codes);
         cudaFree(sl.factors);
         cudaFree(sl.O);
+        cudaFree(sl.err_dev);
+        if (sl.err_host) cudaFreeHost(sl.err_host);
     }
     s->slots.clear();
 }
@@ -258,7 +272,10 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
             cudaMalloc(&sl.X, sizeof(float) * rows * dmax) != cudaSuccess ||
             cudaMalloc(&sl.codes, std::max<size_t>(16, cbmax * rows)) != cudaSuccess ||
             cudaMalloc(&sl.factors, sizeof(float) * rows * nfmax) != cudaSuccess ||
-            cudaMalloc(&sl.O, scrmax) != cudaSuccess) {
+            cudaMalloc(&sl.O, scrmax) != cudaSuccess ||
+            cudaMalloc(&sl.err_dev, sizeof(int)) != cudaSuccess ||
+            cudaMemset(sl.err_dev, 0, sizeof(int)) != cudaSuccess ||
+            cudaHostAlloc(&sl.err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
             free_slots(s);
             delete s;
             return set_error(SAQ_ERR_OOM, "slot allocation failed");
@@ -329,7 +346,8 @@ saq_status saq_ingest_wait(saq_ingest *s, uint64_t ticket, int32_t timeout_ms, d
     const saq_status st = r->status;
     s->reqs.erase(it);
     delete r;
-    if (st != SAQ_OK) return set_error(st, "request failed on the device");
+    if (st != SAQ_OK)
+        return set_error(st, "request failed on the device: %s", saq_status_string(st));
     return SAQ_OK;
 }
 

@@ -116,6 +116,8 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t s);
 void model_release_device(saq_model *m);
 
 // ---------------------------------------------------------------- kernels
+// Models per grouped launch (a serving batch of several collections).
+constexpr int kMaxGroups = 4;
 // Layout of projected rows: row-major (ldo floats per row) or interleaved by
 // groups of 32 rows, O_i[((row / 32) * dk + col) * 32 + row % 32] (the layout
 // the quantize kernel reads; ldo is ignored).
@@ -127,15 +129,36 @@ saq_status launch_project_simt(const saq_model *m, const float *X, int64_t n,
 // interleaved layout and vmax != NULL it also writes, per row and kept
 // segment, max |o| into vmax (interleaved like O: [(row/32) * nk + s] * 32 +
 // row % 32; the caller zeroes it first).
+// err: the device error word the launch raises (bounded waits that gave up,
+// input rows out of range); NULL selects the model's own word.
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n,
                              float *O, int64_t ldo, int layout, float *norms2,
-                             int64_t norms_stride, float *vmax, cudaStream_t s);
+                             int64_t norms_stride, float *vmax, int *err, cudaStream_t s);
 SegCols seg_cols(const saq_model *m);
+// One model's rows of a grouped projection launch (interleaved output, v_max
+// zeroed by the caller, |x - c|^2 into norms[i * nstride]).
+struct ProjJob {
+    const saq_model *m;
+    const float *X;
+    int64_t n;
+    float *O;
+    float *norms;
+    int64_t nstride;
+    float *vmax;
+    int *err;  // NULL: the model's own error word
+};
+// Up to kMaxGroups models of one tensor-core precision in one launch.
+saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, cudaStream_t s);
 bool tc_supported(const saq_model *m);
 void tc_release(saq_model *m);
-// Reads and clears the device error word of the tensor-core projection
-// (synchronises `s`); SAQ_ERR_TIMEOUT if a bounded wait gave up.
+// Reads and clears the model's device error word of the tensor-core
+// projection (synchronises `s`): SAQ_ERR_TIMEOUT if a bounded wait gave up,
+// SAQ_ERR_RANGE if an input row was out of range.
 saq_status tc_check_error(const saq_model *m, cudaStream_t s);
+// The status (and message) of a value read from an error word.
+saq_status tc_error_status(int code);
+// The model's own error word (NULL without tensor-core operands).
+int *tc_error_word(const saq_model *m);
 // norms2[i * stride] = |x_i - c|^2
 saq_status launch_rownorm2(const saq_model *m, const float *X, int64_t n,
                            float *out, int64_t stride, cudaStream_t s);
@@ -146,6 +169,18 @@ saq_status launch_copy_strided(const float *src, int64_t sstride, float *dst,
 // projected rows Oi, with a byte scratch cs of the same layout (k_caq1.cu).
 saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
                        const float *vmax, uint8_t *codes, float *factors, cudaStream_t s);
+// Several models' rows in one launch (a batch of several collections): each
+// job as for launch_caq1.  At most kMaxGroups jobs.
+struct CaqJob {
+    const saq_model *m;
+    const float *Oi;
+    int64_t n;
+    uint8_t *cs;
+    const float *vmax;
+    uint8_t *codes;
+    float *factors;
+};
+saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s);
 // vmax of every (row, kept segment) from interleaved rows Oi (k_caq1.cu).
 // Lane-steps per second of the adjustment step on register-resident data
 // (saq_quantize_step_ceiling).
@@ -161,13 +196,18 @@ size_t encode_scratch_bytes(const saq_model *m, int64_t rows);
 // Projection of rows [0, n) (saq_encode.cu); vmax as for launch_project_tc
 // (may be NULL).
 saq_status project_rows(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                        int layout, float *norms, int64_t nstride, float *vmax, cudaStream_t s);
+                        int layout, float *norms, int64_t nstride, float *vmax, cudaStream_t s,
+                        int *err = nullptr);
 // Quantization of rows [0, n) from interleaved projected rows in `scratch`.
 saq_status quantize_rows(const saq_model *m, void *scratch, int64_t rows_cap, int64_t n,
                          uint8_t *codes, float *factors, cudaStream_t s);
 // The whole encode of rows [0, n) with a scratch for `rows` rows.
+// err as for launch_project_tc.
 saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *codes,
-                       float *factors, void *scratch, int64_t rows, cudaStream_t s);
+                       float *factors, void *scratch, int64_t rows, cudaStream_t s,
+                       int *err = nullptr);
+// 1 if the model's encode runs the tensor-core projection.
+bool use_tc(const saq_model *m);
 // Estimator.
 saq_status launch_estimate_staged(const saq_model *m, const uint8_t *codes, const float *factors,
                                   int64_t n, const float *Q, const float *Qrot, const float *qn2,

@@ -49,6 +49,14 @@ extern "C" saq_status saq_encode_noalloc(const saq_model *m, const float *X_dev,
         return set_error(SAQ_ERR_INVALID, "NULL buffer");
     if (((uintptr_t)X_dev | (uintptr_t)codes_dev | (uintptr_t)factors_dev) & 15u)
         return set_error(SAQ_ERR_INVALID, "device buffers must be 16-byte aligned");
+    int dev = -1;
+    SAQ_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev != m->device)
+        return set_error(SAQ_ERR_INVALID, "model lives on device %d, current device is %d",
+                         m->device, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    // a model without kept dimensions needs no scratch, whatever n is
+    if (m->dk == 0) return launch_rownorm2(m, X_dev, n, factors_dev, m->nf, s);
     if (encode_scratch_bytes(m, n) > kScratchBytes) {
         int64_t most = 0;
         while (encode_scratch_bytes(m, most + 32) <= kScratchBytes) most += 32;
@@ -57,13 +65,6 @@ extern "C" saq_status saq_encode_noalloc(const saq_model *m, const float *X_dev,
                          "%zu bytes (at most %lld rows for this model)",
                          (long long)n, m->dk, kScratchBytes, (long long)most);
     }
-    int dev = -1;
-    SAQ_CUDA_CHECK(cudaGetDevice(&dev));
-    if (dev != m->device)
-        return set_error(SAQ_ERR_INVALID, "model lives on device %d, current device is %d",
-                         m->device, dev);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (m->dk == 0) return launch_rownorm2(m, X_dev, n, factors_dev, m->nf, s);
     float *O = nullptr;
     saq_status st = scratch_address(dev, &O);
     if (st != SAQ_OK) return st;

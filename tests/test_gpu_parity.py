@@ -1,14 +1,5 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
-same seeded inputs.
-
-Bars (FP32 path):
-  * >= 99.9% of codes identical, and every vector-segment with a mismatching
-    code has an oracle decision margin < 1e-5 (cosine units for adjustment
-    trials, |o| units for initial-code interval boundaries);
-  * per-vector relative quantization error within 1e-4 of the oracle's;
-  * |o_s| within 1e-5 relative, cos_s within 1e-5;
-  * mean relative distance-estimate error within 1e-4 of the oracle's.
-"""
+same seeded inputs (bars in tests/parity_check.py)."""
 import numpy as np
 import pytest
 import torch
@@ -16,13 +7,9 @@ import torch
 import oracle as O
 import paper_2509_12086_gb300 as P
 from paper_2509_12086_gb300 import synth
+from tests.parity_check import DIST_TOL, check_codes, gpu_codes_by_round
 
 pytestmark = pytest.mark.gpu
-
-CODE_AGREE = 0.999
-MARGIN = 1e-5
-EPS_TOL = 1e-4
-DIST_TOL = 1e-4
 
 
 def lib_model(mo, precision="fp32", rounds=6):
@@ -34,46 +21,15 @@ def precisions():
     return ["fp32_simt", "fp32"]
 
 
-def check_codes(mo, eo, codes_gpu, factors_gpu, agree_min=CODE_AGREE, margin=MARGIN):
-    """Codes and factors against the oracle.
-
-    Where a vector-segment's codes all agree, its factors must agree tightly.
-    A vector-segment with a mismatch must have an oracle decision margin below
-    `margin` (a near-tie that FP32 may resolve the other way); past such a
-    decision both trajectories are correct CAQ results, so there the GPU
-    result is checked for validity instead: its cosine is at least the
-    initial code's (to the 1e-5 of the FP32 factor) and within 1e-3 of the
-    oracle's.  The per-vector error
-    bar applies to every vector without an excused mismatch."""
-    codes = O.unpack(codes_gpu, mo)
-    # padding bits of the packed planes are zero: pack(unpack(x)) == x
-    assert np.array_equal(O.pack(codes, mo), codes_gpu)
-    eq = codes == eo.codes
-    frac = eq.mean() if eq.size else 1.0
-    assert frac >= agree_min, "code agreement %.6f" % frac
-    k = len(mo.kept)
-    mism = np.zeros((codes.shape[0], k), dtype=bool)
-    for j, (off, l, b) in enumerate(mo.kept):
-        mism[:, j] = ~eq[:, off:off + l].all(axis=1)
-    if mism.any():
-        worst = eo.min_margin[mism].max()
-        assert worst < margin, "mismatch at oracle margin %.3g" % worst
-    f = factors_gpu.astype(np.float64)
-    ref = eo.factors
-    nr_g, nr_o = f[:, 1::2], ref[:, 1::2]
-    assert np.allclose(nr_g, nr_o, rtol=1e-5, atol=1e-6 * max(1.0, nr_o.max()))
-    assert np.allclose(f[:, 0], ref[:, 0], rtol=1e-5, atol=1e-6 * max(1.0, ref[:, 0].max()))
-    cg, co = f[:, 2::2], ref[:, 2::2]
-    assert np.all((np.abs(cg - co) <= 1e-5) | mism), "cos factor off where codes agree"
-    if mism.any():
-        # the FP32 cosine factor carries ~1e-6 rounding per 1000 coordinates
-        assert np.all(cg[mism] >= eo.init_cos[mism] - 1e-5)
-        assert np.all(np.abs(cg[mism] - co[mism]) <= 1e-3)
-    clean = ~mism.any(axis=1)
-    eg, eo_ = O.quant_error(f, mo), O.quant_error(ref, mo)
-    assert np.max(np.abs(eg - eo_)[clean], initial=0.0) <= EPS_TOL
-    assert abs(eg.mean() - eo_.mean()) <= EPS_TOL
-    return frac, mism.mean() if mism.size else 0.0
+def check_encode(mo, m, X, rounds=6, label="", **kw):
+    """Encode host rows X with model m on the GPU and check the result
+    against the oracle's encode of the same rows."""
+    eo = O.encode(X, mo, rounds=rounds)
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    codes, factors = m.encode(Xd)
+    after = lambda: gpu_codes_by_round(m, mo, lambda: m.encode(Xd)[0].cpu().numpy(), rounds)
+    return check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(),
+                       O_rows=O.project(X, mo)[0], after=after, rounds=rounds, label=label, **kw)
 
 
 @pytest.fixture(scope="module")
@@ -89,9 +45,7 @@ def c1():
 @pytest.mark.parametrize("prec", precisions())
 def test_c1_encode_parity(c1, prec):
     X, Qm, mo, eo = c1
-    m = lib_model(mo, prec)
-    codes, factors = m.encode(torch.from_numpy(X).cuda())
-    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy())
+    check_encode(mo, lib_model(mo, prec), X, label="c1_d128 %s" % prec)
 
 
 def test_c1_quantize_only_parity(c1):
@@ -103,10 +57,12 @@ def test_c1_quantize_only_parity(c1):
     O32 = Oo.astype(np.float32)
     eo = O.encode_projected(O32.astype(np.float64), n2, mo, rounds=6)
     m = lib_model(mo)
-    codes, factors = m.quantize_projected(torch.from_numpy(O32).cuda(),
-                                          torch.from_numpy(n2.astype(np.float32)).cuda())
-    frac, _ = check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(),
-                          agree_min=0.9999, margin=1e-6)
+    Od = torch.from_numpy(O32).cuda()
+    nd = torch.from_numpy(n2.astype(np.float32)).cuda()
+    codes, factors = m.quantize_projected(Od, nd)
+    after = lambda: gpu_codes_by_round(m, mo, lambda: m.quantize_projected(Od, nd)[0].cpu().numpy(), 6)
+    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(), O_rows=O32.astype(np.float64),
+                after=after, agree_min=0.9999, margin=1e-6, label="c1_d128 quantize-only")
 
 
 def test_c1_estimator_parity(c1):
@@ -153,10 +109,7 @@ def test_edge_plans_and_ragged_rows(prec, n):
     rng = np.random.default_rng(n)
     X = (rng.standard_normal((n, 200)) * np.linspace(1, 0.1, 200)).astype(np.float32)
     X[:: 5] = mo.mean.astype(np.float32)
-    eo = O.encode(X, mo, rounds=6)
-    m = lib_model(mo, prec)
-    codes, factors = m.encode(torch.from_numpy(X).cuda())
-    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(), agree_min=0.999)
+    check_encode(mo, lib_model(mo, prec), X, label="edge plans n=%d %s" % (n, prec))
 
 
 def test_zero_rows_and_empty_call():
@@ -177,10 +130,7 @@ def test_long_segment_1024():
     mo = _random_model(1024, plan, seed=3)
     rng = np.random.default_rng(1)
     X = rng.standard_normal((300, 1024)).astype(np.float32)
-    eo = O.encode(X, mo, rounds=6)
-    m = lib_model(mo)
-    codes, factors = m.encode(torch.from_numpy(X).cuda())
-    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy())
+    check_encode(mo, lib_model(mo), X, label="one 1024-long segment")
 
 
 def test_fit_parity():
@@ -237,7 +187,11 @@ def test_c2_full_size_sampled_rows():
     it = torch.from_numpy(idx).cuda()
     Xs = X[it].cpu().numpy()
     eo = O.encode(Xs, mo, rounds=w["rounds"])
-    check_codes(mo, eo, codes[it].cpu().numpy(), factors[it].cpu().numpy())
+    Xsd = X[it].contiguous()
+    after = lambda: gpu_codes_by_round(m, mo, lambda: m.encode(Xsd)[0].cpu().numpy(), w["rounds"])
+    check_codes(mo, eo, codes[it].cpu().numpy(), factors[it].cpu().numpy(),
+                O_rows=O.project(Xs, mo)[0], after=after, rounds=w["rounds"],
+                label="c2_d960 fp32 (20,000 of 1,000,000 rows)")
     Qm = synth.queries(10000, d, w["alpha"]).numpy()
     sub = idx[:1000]
     ex = O.exact_dist(Xs[:1000], Qm)
@@ -413,22 +367,31 @@ def test_host_path_several_chunks_equals_device_encode():
     assert torch.equal(fh, fd.cpu())
 
 
-@pytest.mark.parametrize("d,tc", [(6144, True), (6400, False)])
-def test_largest_dimensions(d, tc):
+@pytest.mark.parametrize("d", [6144, 6400])
+def test_largest_dimensions(d):
     """d = 6144 is the largest dimension the tensor-core projection takes
     (the centring term of a whole row sits in shared memory beside the
-    stages); beyond it an FP32 model projects on the CUDA cores.  Both
-    encodes agree with the oracle."""
+    stages).  Beyond it a tensor-core precision is refused with
+    SAQ_ERR_UNSUPPORTED, explicitly (no silent switch of the projection),
+    and the CUDA-core projection (fp32_simt) must be chosen; both encodes
+    agree with the oracle."""
     plan = [(0, 1024, 4), (1024, 2048, 2), (3072, d - 3072, 1)]
     mo = _random_model(d, plan, seed=d)
     rng = np.random.default_rng(d)
     X = (rng.standard_normal((300, d)) * np.linspace(1, 0.05, d)).astype(np.float32)
-    m = lib_model(mo, "fp32")
-    assert m.tensor_cores == tc
-    codes, factors = m.encode(torch.from_numpy(X).cuda())
+    if d > 6144:
+        with pytest.raises(P.SaqError, match="unsupported"):
+            lib_model(mo, "fp32")
+        m = lib_model(mo, "fp32_simt")
+        assert not m.tensor_cores
+        with pytest.raises(P.SaqError, match="unsupported"):
+            m.set_precision("bf16")
+        assert not m.tensor_cores  # a refused precision leaves the model as it was
+    else:
+        m = lib_model(mo, "fp32")
+        assert m.tensor_cores
+    check_encode(mo, m, X, label="d=%d" % d)
     m.check_device()
-    eo = O.encode(X, mo, rounds=6)
-    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy())
 
 
 def test_more_kept_segments_than_supported_is_an_error():
@@ -453,7 +416,4 @@ def test_odd_segment_lengths(prec):
     mo = _random_model(128, plan, seed=5)
     rng = np.random.default_rng(17)
     X = (rng.standard_normal((1000, 128)) * np.linspace(1, 0.1, 128)).astype(np.float32)
-    eo = O.encode(X, mo, rounds=6)
-    m = lib_model(mo, prec)
-    codes, factors = m.encode(torch.from_numpy(X).cuda())
-    check_codes(mo, eo, codes.cpu().numpy(), factors.cpu().numpy(), agree_min=0.999)
+    check_encode(mo, lib_model(mo, prec), X, label="odd segment lengths %s" % prec)
