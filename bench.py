@@ -336,7 +336,9 @@ def run_reference(args):
         return
     import oracle as O
     w = dict(synth.WORKLOADS[args.workload])
-    X = synth.power_law(min(w["n"], 60000), w["d"], w["alpha"]).numpy()
+    # model fitted on 50,000 rows (not timed); each step encodes a chunk of
+    # ref_rows further rows, the chunk size of the CPU baseline
+    X = synth.power_law(min(w["n"], 50000 + args.ref_rows), w["d"], w["alpha"]).numpy()
     mo = O.fit(X[:50000], w["avg_bits"])
     sample = X[50000:50000 + args.ref_rows] if X.shape[0] > 50000 else X[:args.ref_rows]
     for _ in range(args.warmup):
@@ -612,13 +614,15 @@ def serving_run(args, dev):
     service's capacity on this mix is measured first (all requests submitted
     at once, copies included, median of three passes); then the same requests
     arrive as a Poisson stream at a load factor of that capacity, three runs
-    per load factor.  HBM budget 40 GB."""
+    per load factor.  HBM budget 40 GB.  Projection in BF16 (the serving
+    configuration); the same requests through the FP32 projection are
+    reported beside it (capacity and the headline load factor)."""
     rng = np.random.default_rng(2024)
     specs = [(128, 4.0), (960, 4.0), (1536, 2.0)]
     models = []
     for d, bits in specs:
         Xf = synth.power_law(100_000, d, 0.8, seed=17 + d, device=dev)
-        models.append(P.saq_fit(Xf, avg_bits=bits))
+        models.append(P.saq_fit(Xf, avg_bits=bits, precision=args.ingest_precision))
     total = args.ingest_vectors
     sizes, colls = [], []
     while sum(sizes) < total:
@@ -638,17 +642,19 @@ def serving_run(args, dev):
         svc.wait(t, timeout_ms=120000)
     # capacity of the service on this request mix: everything submitted at
     # once, the median of three passes
-    sat = []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        tk = [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs]
-        for t in tk:
-            svc.wait(t, timeout_ms=120000)
-        sat.append(time.perf_counter() - t0)
-    capacity = sum(sizes) / float(np.median(sat))
+    def capacity_of():
+        sat = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            tk = [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs]
+            for t in tk:
+                svc.wait(t, timeout_ms=120000)
+            sat.append(time.perf_counter() - t0)
+        return sum(sizes) / float(np.median(sat))
+    capacity = capacity_of()
     # Poisson arrivals at load factors rho of that capacity (the headline
     # figures are those of --ingest-load; 0.5 and 0.95 are reported beside)
-    def poisson(rho, seed):
+    def poisson(rho, seed, capacity=capacity):
         rate = rho * capacity / float(np.mean(sizes))  # requests / s
         gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=len(sizes))
         b0 = svc.stats()["batches"]
@@ -670,19 +676,37 @@ def serving_run(args, dev):
                 "batches": int(svc.stats()["batches"] - b0)}
     # each load factor three times (a run lasts 0.05-0.1 s, so one hiccup of
     # the host can decide it): the run with the median p99, and all three
-    def median_run(rho, seed):
-        runs = sorted((poisson(rho, seed + 100 * k) for k in range(3)), key=lambda r: r["p99_ms"])
+    def median_run(rho, seed, capacity=capacity):
+        runs = sorted((poisson(rho, seed + 100 * k, capacity) for k in range(3)),
+                      key=lambda r: r["p99_ms"])
         out = dict(runs[1])
         out["runs_p50_p99_ms"] = [[r["p50_ms"], r["p99_ms"]] for r in runs]
         return out
     head = median_run(args.ingest_load, 2025)
     others = {("%.2f" % rho): median_run(rho, 2026 + k)
               for k, rho in enumerate((0.5, 0.95)) if abs(rho - args.ingest_load) > 1e-9}
+    st = svc.stats()
+    batch_stats = {k: st[k] for k in ("batches", "mixed_batches", "deferred_batches",
+                                      "peak_bytes_in_flight")}
     svc.close()
-    out = {"requests": len(sizes), "vectors": int(sum(sizes)), "saturation_vectors_per_s": capacity}
+    # the same requests through the FP32 projection, beside
+    fp32 = None
+    if args.ingest_precision != "fp32":
+        for m in models:
+            m.set_precision("fp32")
+        svc = P.Ingest(models, hbm_budget_bytes=40 << 30, max_batch_rows=65536, slots=4)
+        for t in [svc.submit(c, Xr, cb, fb) for c, Xr, cb, fb in reqs[:30]]:
+            svc.wait(t, timeout_ms=120000)
+        cap32 = capacity_of()
+        fp32 = {"saturation_vectors_per_s": cap32}
+        fp32.update(median_run(args.ingest_load, 2125, cap32))
+        svc.close()
+    out = {"requests": len(sizes), "vectors": int(sum(sizes)), "saturation_vectors_per_s": capacity,
+           "projection": args.ingest_precision}
     out.update(head)
     out.update({"other_loads": others, "slots": 4, "max_batch_rows": 65536, "hbm_budget_gb": 40,
-                "collections": "d128@4b, d960@4b, d1536@2b (alpha 0.8)"})
+                "collections": "d128@4b, d960@4b, d1536@2b (alpha 0.8)",
+                "batch_stats": batch_stats, "fp32_projection": fp32})
     return out
 
 
@@ -703,7 +727,7 @@ def main():
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--e2e-rows", type=int, default=1_000_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--ref-rows", type=int, default=4000)
+    ap.add_argument("--ref-rows", type=int, default=100000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
@@ -711,6 +735,7 @@ def main():
     ap.add_argument("--no-estimator", action="store_true")
     ap.add_argument("--ingest-vectors", type=int, default=2_000_000)
     ap.add_argument("--ingest-load", type=float, default=0.8)
+    ap.add_argument("--ingest-precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -305,34 +305,49 @@ saq_status saq_set_wait_limit(uint64_t ns);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous-batching ingest over several resident collections.
- * (The paper's encoder is offline; this runtime applies saq_encode to a
- * stream of insert requests.)
+ * (The paper's encoder is offline; this runtime applies the encode of
+ * saq_encode to a stream of insert requests.)
  *
  * Each collection is a fitted model kept resident on the device.  Requests
- * (host rows of one collection) queue on submit; a scheduler thread packs
- * queued requests of one collection, oldest first, into batches of at most
- * max_batch_rows rows (large requests are split across batches) and runs each
- * batch on one of `slots` streams: copy-in, the encode kernels, copy-out.  A
- * request that arrives while others are on the GPU joins the next batch of its
- * collection as soon as a slot is free, so batches of different collections
- * and the copies of one batch overlap the encode of another.  Admission is by
- * HBM budget: slot buffers (inputs, codes, factors, projection scratch) are
- * allocated once at open, and open fails with SAQ_ERR_OOM if `slots` slots do
- * not fit in hbm_budget_bytes.  Results are identical to saq_encode on the
- * same rows: every row is encoded independently.
+ * (host rows of one collection) queue on submit; a scheduler thread forms
+ * batches as slots free up: a batch takes the queued requests oldest first,
+ * from up to 4 collections whose models use the same tensor-core precision,
+ * at most max_batch_rows rows in all (large requests are split across
+ * batches), and encodes them with ONE projection launch and ONE
+ * quantize/adjust/pack launch over all its collections, on one of `slots`
+ * streams, between one copy-in and one copy-out per request piece.  A model
+ * on the CUDA-core projection gets batches of its own.  Requests that arrive
+ * while others are on the GPU join the next batch, so the copies and kernels
+ * of different batches overlap.
+ * Admission is by HBM budget: a batch's device memory (inputs, codes,
+ * factors and projection scratch: 4 d + code_bytes + 4 factor_count bytes per
+ * row plus the encode's scratch) is taken from the library's stream-ordered
+ * pool when the batch is formed and returned when it completes, and a batch
+ * is formed only with the pieces of requests that fit in hbm_budget_bytes
+ * beside the batches already in flight (a request that does not fit waits,
+ * whole or in part, for earlier batches to complete; each time the budget
+ * holds back queued work counts as a deferred batch).  Open fails with
+ * SAQ_ERR_OOM if one batch of max_batch_rows rows of some collection alone
+ * exceeds the budget.  Results are identical to saq_encode on the same rows:
+ * every row is encoded independently.  A bounded wait of a batch's
+ * projection that gave up (SAQ_ERR_TIMEOUT) or an input row out of range
+ * (SAQ_ERR_RANGE) fails every request with rows in that batch.
  * ------------------------------------------------------------------------ */
 typedef struct saq_ingest saq_ingest;
 
 typedef struct {
-    size_t hbm_budget_bytes;  /* device memory the service may hold       */
-    int32_t max_batch_rows;   /* rows per batch launch (>= 1)              */
-    int32_t slots;            /* concurrent batches (streams), >= 1        */
+    size_t hbm_budget_bytes;  /* device memory the batches in flight may hold */
+    int32_t max_batch_rows;   /* rows per batch (>= 1), over all its collections */
+    int32_t slots;            /* concurrent batches (streams), 1..64          */
 } saq_ingest_params;
 
 typedef struct {
     uint64_t submitted, completed, rows_completed, batches;
     double p50_latency_s, p99_latency_s, max_latency_s;  /* submit -> done */
     double busy_s;            /* wall time between first submit and last completion */
+    uint64_t mixed_batches;   /* batches that held rows of several collections */
+    uint64_t deferred_batches;/* times queued work waited for budget          */
+    size_t peak_bytes_in_flight; /* most device memory the batches held at once */
 } saq_ingest_stats;
 
 /* models[n_models] stay owned by the caller and must outlive the service. */
@@ -393,7 +408,7 @@ int32_t saq_model_has_basis(const saq_model *m);
 /* Instruction ceiling of the code adjustment (diagnostic; no counterpart in
  * the paper).  Runs the adjustment's own per-coordinate step (Algorithm 1 in
  * the closed form of saq_encode) on coordinates held in registers, with no
- * memory traffic, at warps_per_sm resident warps per SM (8, 16, ..., 64;
+ * memory traffic, at warps_per_sm resident warps per SM (4, 8, ..., 64;
  * the quantize kernel runs at 32) and B = bits, on the current device and
  * the legacy default stream, and writes the lane-steps per second
  * (coordinate trials of one vector-segment each) to *lane_steps_per_s.

@@ -50,7 +50,9 @@ class saq_ingest_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("rows_completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
-                ("max_latency_s", ctypes.c_double), ("busy_s", ctypes.c_double)]
+                ("max_latency_s", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("mixed_batches", ctypes.c_uint64), ("deferred_batches", ctypes.c_uint64),
+                ("peak_bytes_in_flight", ctypes.c_size_t)]
 
 
 class saq_params(ctypes.Structure):

@@ -365,8 +365,8 @@ k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch) {
 
 // The instruction ceiling of the adjustment: caq_step on coordinates held in
 // registers (no loads or stores), kU per lane, a sign flip per step keeping
-// moves happening; one block of 256 threads per 8 warps of occupancy.
-__global__ void __launch_bounds__(256) k_step_ceiling(int iters, int cmax, float *out) {
+// moves happening; one block of 128 threads per 4 warps of occupancy.
+__global__ void __launch_bounds__(128) k_step_ceiling(int iters, int cmax, float *out) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     float x[kU];
     int c[kU];
@@ -509,19 +509,19 @@ saq_status step_ceiling(int warps_per_sm, int bits, double *lane_steps_per_s) {
     int dev = 0, sms = 0;
     SAQ_CUDA_CHECK(cudaGetDevice(&dev));
     SAQ_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int blocks = sms * (warps_per_sm / 8);
+    const int blocks = sms * (warps_per_sm / 4);
     const int iters = 2000;
     float *out = nullptr;
-    SAQ_CUDA_CHECK(scratch_alloc((void **)&out, sizeof(float) * (size_t)blocks * 256, 0));
+    SAQ_CUDA_CHECK(scratch_alloc((void **)&out, sizeof(float) * (size_t)blocks * 128, 0));
     cudaEvent_t a = nullptr, b = nullptr;
     saq_status st = SAQ_OK;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         st = set_error(SAQ_ERR_CUDA, "event creation failed");
     } else {
         const int cmax = (1 << bits) - 1;
-        k_step_ceiling<<<blocks, 256>>>(iters / 4, cmax, out);  // warm-up
+        k_step_ceiling<<<blocks, 128>>>(iters / 4, cmax, out);  // warm-up
         cudaEventRecord(a, 0);
-        k_step_ceiling<<<blocks, 256>>>(iters, cmax, out);
+        k_step_ceiling<<<blocks, 128>>>(iters, cmax, out);
         cudaEventRecord(b, 0);
         note_launches(2);
         float ms = 0.f;
@@ -529,7 +529,7 @@ saq_status step_ceiling(int warps_per_sm, int bits, double *lane_steps_per_s) {
             cudaGetLastError() != cudaSuccess || ms <= 0.f)
             st = set_error(SAQ_ERR_CUDA, "step-ceiling measurement failed");
         else
-            *lane_steps_per_s = (double)blocks * 256.0 * iters * kU / (ms * 1e-3);
+            *lane_steps_per_s = (double)blocks * 128.0 * iters * kU / (ms * 1e-3);
     }
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);

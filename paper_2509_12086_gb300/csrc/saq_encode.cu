@@ -109,6 +109,36 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
     return SAQ_OK;
 }
 
+// Rows of up to kMaxGroups models in one projection launch and one quantize
+// launch (a serving batch of several collections); see saq_internal.h.
+saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err) {
+    if (njobs < 1 || njobs > kMaxGroups)
+        return set_error(SAQ_ERR_INVALID, "1..%d models per grouped encode", kMaxGroups);
+    ProjJob pj[kMaxGroups];
+    CaqJob cj[kMaxGroups];
+    int np = 0;
+    for (int i = 0; i < njobs; ++i) {
+        const EncodeJob &j = jobs[i];
+        if (j.n <= 0) continue;
+        if (j.m->dk == 0) {
+            saq_status st = launch_rownorm2(j.m, j.X, j.n, j.factors, j.m->nf, s);
+            if (st != SAQ_OK) return st;
+            continue;
+        }
+        if (!use_tc(j.m))
+            return set_error(SAQ_ERR_INVALID, "grouped encode needs tensor-core models");
+        const ScratchParts p = scratch_parts(j.m, j.scratch, j.n);
+        SAQ_CUDA_CHECK(cudaMemsetAsync(p.vmax, 0, p.vmax_bytes, s));
+        pj[np] = ProjJob{j.m, j.X, j.n, p.Oi, j.factors, j.m->nf, p.vmax, err};
+        cj[np] = CaqJob{j.m, p.Oi, j.n, p.cs, p.vmax, j.codes, j.factors};
+        ++np;
+    }
+    if (np == 0) return SAQ_OK;
+    saq_status st = launch_project_tc_grouped(pj, np, s);
+    if (st != SAQ_OK) return st;
+    return launch_caq1_grouped(cj, np, s);
+}
+
 }  // namespace saq
 
 using namespace saq;
@@ -391,8 +421,8 @@ saq_status saq_quantize_step_ceiling(int32_t warps_per_sm, int32_t bits,
                                      double *lane_steps_per_s) {
     clear_error();
     if (!lane_steps_per_s) return set_error(SAQ_ERR_INVALID, "NULL output");
-    if (warps_per_sm < 8 || warps_per_sm > 64 || warps_per_sm % 8 != 0)
-        return set_error(SAQ_ERR_INVALID, "warps_per_sm must be 8, 16, ..., 64");
+    if (warps_per_sm < 4 || warps_per_sm > 64 || warps_per_sm % 4 != 0)
+        return set_error(SAQ_ERR_INVALID, "warps_per_sm must be 4, 8, ..., 64");
     if (bits < 1 || bits > 8) return set_error(SAQ_ERR_INVALID, "bits outside 1..8");
     return step_ceiling(warps_per_sm, bits, lane_steps_per_s);
 }

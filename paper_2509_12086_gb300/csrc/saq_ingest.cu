@@ -1,9 +1,14 @@
 // saq_ingest.cu -- serving runtime: continuous batching of insert requests
 // over several resident collections (see include/saq.h).
 //
-// Host side only; the device work of a batch is the encode of saq_encode
-// (projection + quantize/adjust/pack kernels) on the batch's slot stream,
-// between an H2D copy per request piece and a D2H copy per piece.
+// Host side only.  A batch takes request pieces of up to kMaxGroups
+// collections whose models share the tensor-core precision; its device work
+// is one H2D copy per piece, ONE projection launch and ONE quantize launch
+// over all its collections (encode_grouped), and one D2H copy per piece, on
+// the batch's slot stream.  Its device memory (inputs, codes, factors,
+// projection scratch) comes from the library's stream-ordered pool when the
+// batch is formed and goes back when it completes; a batch is formed only
+// if that memory fits in the HBM budget beside the batches in flight.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -34,20 +39,43 @@ struct Request {
 
 struct Piece {
     Request *req;
-    int64_t r0, nr, off;  // rows [r0, r0 + nr) of req at batch row `off`
+    int group;        // index into the batch's groups
+    int64_t r0, nr;   // rows [r0, r0 + nr) of req ...
+    int64_t off;      // ... at row `off` of its group
+};
+
+// One collection's rows of a batch, and their device regions.
+struct Group {
+    int coll = 0;
+    int64_t rows = 0;
+    float *X = nullptr;
+    uint8_t *codes = nullptr;
+    float *factors = nullptr;
+    void *scratch = nullptr;
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    float *X = nullptr, *factors = nullptr;
-    void *O = nullptr;
-    uint8_t *codes = nullptr;
     int *err_dev = nullptr;   // the batch's device error word (bounded waits, input range)
     int *err_host = nullptr;  // its copy, written on the slot stream before the callback
+    uint8_t *buf = nullptr;   // the batch's device memory (library pool)
+    size_t bytes = 0;         // ... as reserved against the budget
     bool busy = false;
     bool finished = false;  // set by the stream callback
     std::vector<Piece> pieces;
+    std::vector<Group> groups;
 };
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device bytes of `rows` rows of model m in a batch.
+size_t group_bytes(const saq_model *m, int64_t rows) {
+    if (rows <= 0) return 0;
+    const size_t r = (size_t)rows;
+    return align256(sizeof(float) * r * (size_t)m->d) + align256(m->code_bytes * r) +
+           align256(sizeof(float) * r * (size_t)m->nf) +
+           (m->dk > 0 ? align256(saq::encode_scratch_bytes(m, rows)) : 0);
+}
 
 }  // namespace
 
@@ -63,9 +91,12 @@ struct saq_ingest {
     uint64_t next_ticket = 1;
     bool stopping = false;
     std::thread th;
+    size_t in_flight = 0;  // device bytes of the batches in flight
     // statistics
     std::vector<double> lat;
     uint64_t submitted = 0, completed = 0, rows_completed = 0, batches = 0;
+    uint64_t mixed = 0, deferred = 0;
+    size_t peak = 0;
     double max_lat = 0;
     bool any_submit = false;
     Clock::time_point t_first, t_last;
@@ -116,67 +147,169 @@ void reap(saq_ingest *s) {
                 s->t_last = now;
             }
         }
+        s->in_flight -= sl.bytes;  // the batch's memory went back on its stream
+        sl.bytes = 0;
+        sl.buf = nullptr;
         sl.pieces.clear();
+        sl.groups.clear();
         sl.busy = false;
         sl.finished = false;
     }
     s->cv_done.notify_all();
 }
 
-// Pick the collection whose oldest queued request is the oldest overall.
-int pick_collection(saq_ingest *s) {
-    int best = -1;
-    Clock::time_point t{};
-    for (size_t c = 0; c < s->queues.size(); ++c) {
-        if (s->queues[c].empty()) continue;
-        const Clock::time_point tc = s->queues[c].front()->t_submit;
-        if (best < 0 || tc < t) { best = (int)c; t = tc; }
-    }
-    return best;
+// Whether two models' rows may share a grouped launch.
+bool same_class(const saq_model *a, const saq_model *b) {
+    const bool ta = saq::use_tc(a) || a->dk == 0, tb = saq::use_tc(b) || b->dk == 0;
+    if (!ta || !tb) return false;  // a CUDA-core model runs alone
+    return a->dk == 0 || b->dk == 0 || a->tc.precision == b->tc.precision;
 }
 
-// Form a batch for a free slot and enqueue its work.  Caller holds mu.
-void dispatch(saq_ingest *s, Slot &sl, int coll) {
-    saq_model *m = s->models[(size_t)coll];
-    std::deque<Request *> &q = s->queues[(size_t)coll];
-    int64_t rows = 0;
+// Form a batch for the free slot `sl` from the queues and enqueue its work.
+// Requests are taken in arrival order over all collections whose models can
+// share the launch with the oldest request's (up to kMaxGroups collections),
+// at most max_batch_rows rows, and only as much as the HBM budget leaves
+// beside the batches in flight.  Returns false if nothing could be admitted.
+// Caller holds mu.
+bool dispatch(saq_ingest *s, Slot &sl) {
+    const int nc = (int)s->queues.size();
+    // the oldest queued request decides the batch's class
+    int c0 = -1;
+    for (int c = 0; c < nc; ++c)
+        if (!s->queues[(size_t)c].empty() &&
+            (c0 < 0 || s->queues[(size_t)c].front()->t_submit <
+                           s->queues[(size_t)c0].front()->t_submit))
+            c0 = c;
+    if (c0 < 0) return false;
+    const saq_model *m0 = s->models[(size_t)c0];
+    const bool alone = !same_class(m0, m0);  // a CUDA-core model's batch holds it alone
+    const size_t avail = s->p.hbm_budget_bytes > s->in_flight ? s->p.hbm_budget_bytes - s->in_flight : 0;
     const int64_t cap = s->p.max_batch_rows;
-    while (!q.empty() && rows < cap) {
-        Request *r = q.front();
-        const int64_t k = std::min(r->n - r->next_row, cap - rows);
-        sl.pieces.push_back(Piece{r, r->next_row, k, rows});
+    std::vector<int> gidx((size_t)nc, -1);  // collection -> its group in the batch
+    int64_t rows = 0;
+    size_t bytes = 0;  // of all groups
+    while (rows < cap) {
+        // the oldest head request among the collections this batch can take
+        int c = -1;
+        for (int k = 0; k < nc; ++k) {
+            if (s->queues[(size_t)k].empty()) continue;
+            if (alone ? k != c0 : !same_class(m0, s->models[(size_t)k])) continue;
+            if (gidx[(size_t)k] < 0 && (int)sl.groups.size() == saq::kMaxGroups) continue;
+            if (c < 0 || s->queues[(size_t)k].front()->t_submit <
+                             s->queues[(size_t)c].front()->t_submit)
+                c = k;
+        }
+        if (c < 0) break;
+        saq_model *m = s->models[(size_t)c];
+        Request *r = s->queues[(size_t)c].front();
+        const int64_t g_rows = gidx[(size_t)c] < 0 ? 0 : sl.groups[(size_t)gidx[(size_t)c]].rows;
+        const size_t others = bytes - group_bytes(m, g_rows);
+        int64_t k = std::min(r->n - r->next_row, cap - rows);
+        // the most rows of this request that fit in the budget
+        auto fits = [&](int64_t kk) { return others + group_bytes(m, g_rows + kk) <= avail; };
+        bool spent = false;
+        if (!fits(k)) {
+            int64_t lo = 0, hi = k;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) / 2;
+                if (fits(mid)) lo = mid;
+                else hi = mid - 1;
+            }
+            k = lo;
+            spent = true;  // the budget is spent: this is the last piece
+        }
+        if (k == 0) break;
+        if (gidx[(size_t)c] < 0) {
+            gidx[(size_t)c] = (int)sl.groups.size();
+            Group g;
+            g.coll = c;
+            sl.groups.push_back(g);
+        }
+        Group &g = sl.groups[(size_t)gidx[(size_t)c]];
+        sl.pieces.push_back(Piece{r, gidx[(size_t)c], r->next_row, k, g.rows});
         r->next_row += k;
+        g.rows += k;
         rows += k;
-        if (r->next_row == r->n) q.pop_front();
+        bytes = others + group_bytes(m, g.rows);
+        if (r->next_row == r->n) s->queues[(size_t)c].pop_front();
+        if (spent) break;
     }
+    if (sl.groups.empty()) {
+        s->deferred += 1;
+        return false;
+    }
+    // the batch's device memory, from the pool on the slot stream
+    saq_status st = SAQ_OK;
+    void *buf = nullptr;
+    if (saq::scratch_alloc(&buf, bytes, sl.stream) != cudaSuccess) {
+        buf = nullptr;
+        st = SAQ_ERR_OOM;
+    }
+    size_t off = 0;
+    saq::EncodeJob jobs[saq::kMaxGroups];
+    for (size_t i = 0; i < sl.groups.size(); ++i) {
+        Group &g = sl.groups[i];
+        const saq_model *m = s->models[(size_t)g.coll];
+        uint8_t *b = static_cast<uint8_t *>(buf);
+        const size_t r = (size_t)g.rows;
+        g.X = reinterpret_cast<float *>(b + off);
+        off += align256(sizeof(float) * r * (size_t)m->d);
+        g.codes = b + off;
+        off += align256(m->code_bytes * r);
+        g.factors = reinterpret_cast<float *>(b + off);
+        off += align256(sizeof(float) * r * (size_t)m->nf);
+        g.scratch = b + off;
+        off += m->dk > 0 ? align256(saq::encode_scratch_bytes(m, g.rows)) : 0;
+        jobs[i] = saq::EncodeJob{m, g.X, g.rows, g.codes, g.factors, g.scratch};
+    }
+    sl.buf = static_cast<uint8_t *>(buf);
+    sl.bytes = bytes;
     sl.busy = true;
     sl.finished = false;
+    s->in_flight += bytes;
+    s->peak = std::max(s->peak, s->in_flight);
     s->batches += 1;
-    const int d = m->d;
-    const size_t cb = m->code_bytes;
-    const int nf = m->nf;
-    saq_status st = SAQ_OK;
-    for (const Piece &pc : sl.pieces)
-        if (cudaMemcpyAsync(sl.X + pc.off * d, pc.req->X + pc.r0 * d, sizeof(float) * (size_t)pc.nr * d,
-                            cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
-            st = SAQ_ERR_CUDA;
+    if (sl.groups.size() > 1) s->mixed += 1;
+    if (st == SAQ_OK)
+        for (const Piece &pc : sl.pieces) {
+            const Group &g = sl.groups[(size_t)pc.group];
+            const int d = s->models[(size_t)g.coll]->d;
+            if (cudaMemcpyAsync(g.X + pc.off * d, pc.req->X + pc.r0 * d,
+                                sizeof(float) * (size_t)pc.nr * d, cudaMemcpyHostToDevice,
+                                sl.stream) != cudaSuccess)
+                st = SAQ_ERR_CUDA;
+        }
     if (st == SAQ_OK) {
-        if (m->dk == 0) st = saq::launch_rownorm2(m, sl.X, rows, sl.factors, nf, sl.stream);
-        else st = saq::encode_rows(m, sl.X, rows, sl.codes, sl.factors, sl.O, cap, sl.stream,
-                                   sl.err_dev);
+        const saq_model *mg = jobs[0].m;
+        if (sl.groups.size() == 1 && !saq::use_tc(mg)) {
+            // a CUDA-core model (or one without kept dimensions) alone
+            if (mg->dk == 0) st = saq::launch_rownorm2(mg, jobs[0].X, jobs[0].n, jobs[0].factors, mg->nf, sl.stream);
+            else st = saq::encode_rows(mg, jobs[0].X, jobs[0].n, jobs[0].codes, jobs[0].factors,
+                                       jobs[0].scratch, jobs[0].n, sl.stream, sl.err_dev);
+        } else {
+            st = saq::encode_grouped(jobs, (int)sl.groups.size(), sl.stream, sl.err_dev);
+        }
     }
     if (st == SAQ_OK && (cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int),
                                          cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
                          cudaMemsetAsync(sl.err_dev, 0, sizeof(int), sl.stream) != cudaSuccess))
         st = SAQ_ERR_CUDA;
     for (const Piece &pc : sl.pieces) {
+        if (st != SAQ_OK) {
+            pc.req->status = st;
+            continue;
+        }
+        const Group &g = sl.groups[(size_t)pc.group];
+        const saq_model *m = s->models[(size_t)g.coll];
+        const size_t cb = m->code_bytes;
         if (cb)
-            cudaMemcpyAsync(pc.req->codes + pc.r0 * (int64_t)cb, sl.codes + pc.off * (int64_t)cb,
+            cudaMemcpyAsync(pc.req->codes + pc.r0 * (int64_t)cb, g.codes + pc.off * (int64_t)cb,
                             cb * (size_t)pc.nr, cudaMemcpyDeviceToHost, sl.stream);
-        cudaMemcpyAsync(pc.req->factors + pc.r0 * nf, sl.factors + pc.off * nf,
-                        sizeof(float) * (size_t)pc.nr * nf, cudaMemcpyDeviceToHost, sl.stream);
-        if (st != SAQ_OK) pc.req->status = st;
+        cudaMemcpyAsync(pc.req->factors + pc.r0 * m->nf, g.factors + pc.off * m->nf,
+                        sizeof(float) * (size_t)pc.nr * m->nf, cudaMemcpyDeviceToHost, sl.stream);
     }
+    // the memory returns to the pool once the copies out are done
+    if (buf) cudaFreeAsync(buf, sl.stream);
     auto *arg = new std::pair<saq_ingest *, Slot *>(s, &sl);
     if (cudaLaunchHostFunc(sl.stream, on_batch_done, arg) != cudaSuccess) {
         delete arg;
@@ -184,6 +317,7 @@ void dispatch(saq_ingest *s, Slot &sl, int coll) {
         cudaStreamSynchronize(sl.stream);
         sl.finished = true;
     }
+    return true;
 }
 
 void scheduler(saq_ingest *s) {
@@ -193,20 +327,33 @@ void scheduler(saq_ingest *s) {
         reap(s);
         for (Slot &sl : s->slots) {
             if (sl.busy) continue;
-            const int c = pick_collection(s);
-            if (c < 0) break;
-            dispatch(s, sl, c);
+            if (!dispatch(s, sl)) break;  // nothing queued, or no budget left
         }
-        bool busy = false, queued = false;
-        for (Slot &sl : s->slots) busy |= sl.busy;
+        bool busy = false, queued = false, ready = false;
+        for (Slot &sl : s->slots) {
+            busy |= sl.busy;
+            ready |= sl.busy && sl.finished;
+        }
         for (auto &q : s->queues) queued |= !q.empty();
         if (s->stopping && !busy && !queued) break;
-        bool ready = false;
-        for (Slot &sl : s->slots) ready |= (sl.busy && sl.finished);
         if (ready) continue;
-        bool free_slot = false;
-        for (Slot &sl : s->slots) free_slot |= !sl.busy;
-        if (queued && free_slot) continue;
+        if (queued && !busy) {
+            // nothing in flight and still nothing admitted: the budget cannot
+            // hold the head request's next row (open() rules this out)
+            for (auto &q : s->queues)
+                if (!q.empty()) {
+                    Request *r = q.front();
+                    q.pop_front();
+                    r->status = SAQ_ERR_OOM;
+                    r->rows_done = r->n;
+                    r->done = true;
+                    r->t_done = Clock::now();
+                    s->completed += 1;
+                    break;
+                }
+            s->cv_done.notify_all();
+            continue;
+        }
         s->cv_sched.wait(lk);
     }
 }
@@ -217,10 +364,6 @@ void free_slots(saq_ingest *s) {
             cudaStreamSynchronize(sl.stream);
             cudaStreamDestroy(sl.stream);
         }
-        cudaFree(sl.X);
-        cudaFree(sl.codes);
-        cudaFree(sl.factors);
-        cudaFree(sl.O);
         cudaFree(sl.err_dev);
         if (sl.err_host) cudaFreeHost(sl.err_host);
     }
@@ -241,25 +384,24 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
         return set_error(SAQ_ERR_INVALID, "max_batch_rows >= 1 and 1 <= slots <= 64 required");
     int dev = 0;
     SAQ_CUDA_CHECK(cudaGetDevice(&dev));
-    int dmax = 0, dkmax = 0, nfmax = 0;
-    size_t cbmax = 0, scrmax = 0;
+    size_t one_batch = 0;
+    int worst = 0;
     for (int32_t i = 0; i < n_models; ++i) {
         if (!models[i]) return set_error(SAQ_ERR_INVALID, "collection %d is NULL", i);
         if (models[i]->device != dev)
             return set_error(SAQ_ERR_INVALID, "collection %d lives on another device", i);
-        dmax = std::max(dmax, models[i]->d);
-        dkmax = std::max(dkmax, models[i]->dk);
-        nfmax = std::max(nfmax, models[i]->nf);
-        cbmax = std::max(cbmax, models[i]->code_bytes);
-        scrmax = std::max(scrmax, saq::encode_scratch_bytes(models[i], p->max_batch_rows));
+        const size_t b = group_bytes(models[i], p->max_batch_rows);
+        if (b > one_batch) {
+            one_batch = b;
+            worst = i;
+        }
     }
-    const size_t rows = (size_t)p->max_batch_rows;
-    const size_t per_slot = rows * (sizeof(float) * ((size_t)dmax + nfmax) + cbmax) + scrmax +
-                            4 * 256;
-    if (per_slot * (size_t)p->slots > p->hbm_budget_bytes)
+    // admission needs room for at least one whole batch of any collection
+    if (one_batch > p->hbm_budget_bytes)
         return set_error(SAQ_ERR_OOM,
-                         "%d slots of %zu bytes exceed the HBM budget of %zu bytes", p->slots,
-                         per_slot, p->hbm_budget_bytes);
+                         "a batch of %d rows of collection %d (%zu bytes) would exceed the HBM "
+                         "budget of %zu bytes", p->max_batch_rows, worst, one_batch,
+                         p->hbm_budget_bytes);
     saq_ingest *s = new (std::nothrow) saq_ingest();
     if (!s) return set_error(SAQ_ERR_OOM, "host allocation failed");
     s->models.assign(models, models + n_models);
@@ -269,10 +411,6 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
     s->slots.resize((size_t)p->slots);
     for (Slot &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMalloc(&sl.X, sizeof(float) * rows * dmax) != cudaSuccess ||
-            cudaMalloc(&sl.codes, std::max<size_t>(16, cbmax * rows)) != cudaSuccess ||
-            cudaMalloc(&sl.factors, sizeof(float) * rows * nfmax) != cudaSuccess ||
-            cudaMalloc(&sl.O, scrmax) != cudaSuccess ||
             cudaMalloc(&sl.err_dev, sizeof(int)) != cudaSuccess ||
             cudaMemset(sl.err_dev, 0, sizeof(int)) != cudaSuccess ||
             cudaHostAlloc(&sl.err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
@@ -280,6 +418,7 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
             delete s;
             return set_error(SAQ_ERR_OOM, "slot allocation failed");
         }
+        *sl.err_host = 0;
     }
     s->th = std::thread(scheduler, s);
     *out = s;
@@ -366,6 +505,9 @@ saq_status saq_ingest_get_stats(saq_ingest *s, saq_ingest_stats *out) {
         std::nth_element(v.begin(), v.begin() + (long)k, v.end());
         return v[k];
     };
+    out->mixed_batches = s->mixed;
+    out->deferred_batches = s->deferred;
+    out->peak_bytes_in_flight = s->peak;
     out->p50_latency_s = q(0.50);
     out->p99_latency_s = q(0.99);
     out->busy_s = s->completed ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;

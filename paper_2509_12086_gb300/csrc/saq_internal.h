@@ -208,6 +208,21 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
                        int *err = nullptr);
 // 1 if the model's encode runs the tensor-core projection.
 bool use_tc(const saq_model *m);
+// One model's rows of a grouped encode: n <= the rows its scratch holds
+// (encode_scratch_bytes(m, n) bytes).
+struct EncodeJob {
+    const saq_model *m;
+    const float *X;
+    int64_t n;
+    uint8_t *codes;
+    float *factors;
+    void *scratch;
+};
+// The encode of up to kMaxGroups models' rows with one projection launch
+// and one quantize launch; every model with kept dimensions must use the
+// tensor-core projection, all in one precision.  err as for
+// launch_project_tc.
+saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err);
 // Estimator.
 saq_status launch_estimate_staged(const saq_model *m, const uint8_t *codes, const float *factors,
                                   int64_t n, const float *Q, const float *Qrot, const float *qn2,
