@@ -40,12 +40,12 @@ UNIT = "vectors/s"
 # a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "f9ef820d11a2cbfdcee55f35b0ae803b2761020a",
+    "projection": {"src": "k_tc.cu", "sha1": "486ed60328e5b610a47ff5e109b4775b3c319369",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258.195200e6 + 213.691392e6) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ffb094df723d5f82f42d644a9eb4cc3d9a4c3090",
+                   "bytes_per_row": (258205440 + 213139200) / 65536},
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "6f7c9ddcf0d55f2d4437a54be6534436a0fb9ddc",
                              "workload": "c2_d960", "precision": "fp32",
-                             "bytes_per_row": (1981.363e6 + 287.469824e6) / 65536},
+                             "bytes_per_row": (1982832896 + 287276032) / 65536},
 }
 
 
