@@ -468,8 +468,12 @@ class Ingest:
         m = self._models[collection] if 0 <= collection < len(self._models) else None
         cb = m.code_bytes if m is not None else 1
         if codes is None:
-            codes = torch.empty((n, max(cb, 1)), dtype=torch.uint8)
-            factors = torch.empty((n, m.factor_count if m is not None else 1), dtype=torch.float32)
+            # page-locked outputs when the rows are: copies to pageable memory
+            # are synchronous and would serialise the service's batches
+            pin = X.is_pinned()
+            codes = torch.empty((n, max(cb, 1)), dtype=torch.uint8, pin_memory=pin)
+            factors = torch.empty((n, m.factor_count if m is not None else 1), dtype=torch.float32,
+                                  pin_memory=pin)
         t = ctypes.c_uint64()
         _check(load().saq_ingest_submit(self._h, collection, ctypes.c_void_p(X.data_ptr()), n,
                                         ctypes.c_void_p(codes.data_ptr()),

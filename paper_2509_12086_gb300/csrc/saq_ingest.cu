@@ -62,6 +62,7 @@ struct Slot {
     size_t bytes = 0;         // ... as reserved against the budget
     bool busy = false;
     bool finished = false;  // set by the stream callback
+    saq_status launch_status = SAQ_OK;  // an enqueue that failed, applied at completion
     std::vector<Piece> pieces;
     std::vector<Group> groups;
 };
@@ -134,6 +135,7 @@ void reap(saq_ingest *s) {
         for (const Piece &pc : sl.pieces) {
             Request *r = pc.req;
             if (failed) r->status = SAQ_ERR_CUDA;
+            else if (sl.launch_status != SAQ_OK && r->status == SAQ_OK) r->status = sl.launch_status;
             else if (dev_st != SAQ_OK && r->status == SAQ_OK) r->status = dev_st;
             r->rows_done += pc.nr;
             if (r->rows_done == r->n && !r->done) {
@@ -154,24 +156,24 @@ void reap(saq_ingest *s) {
         sl.groups.clear();
         sl.busy = false;
         sl.finished = false;
+        sl.launch_status = SAQ_OK;
     }
     s->cv_done.notify_all();
 }
 
-// Whether two models' rows may share a grouped launch.
-bool same_class(const saq_model *a, const saq_model *b) {
-    const bool ta = saq::use_tc(a) || a->dk == 0, tb = saq::use_tc(b) || b->dk == 0;
-    if (!ta || !tb) return false;  // a CUDA-core model runs alone
-    return a->dk == 0 || b->dk == 0 || a->tc.precision == b->tc.precision;
-}
+// Whether a model's rows may join a grouped launch: a tensor-core model, or
+// one without kept dimensions (only |x - c|^2 is computed for it).  A
+// CUDA-core model's batch holds it alone.
+bool groupable(const saq_model *m) { return saq::use_tc(m) || m->dk == 0; }
 
-// Form a batch for the free slot `sl` from the queues and enqueue its work.
-// Requests are taken in arrival order over all collections whose models can
-// share the launch with the oldest request's (up to kMaxGroups collections),
-// at most max_batch_rows rows, and only as much as the HBM budget leaves
-// beside the batches in flight.  Returns false if nothing could be admitted.
-// Caller holds mu.
-bool dispatch(saq_ingest *s, Slot &sl) {
+// Form a batch for the free slot `sl` from the queues and reserve its device
+// memory against the budget.  Requests are taken in arrival order over all
+// collections whose models can share the launch with the oldest request's
+// (up to kMaxGroups collections), at most max_batch_rows rows, and only as
+// much as the HBM budget leaves beside the batches in flight.  Returns false
+// if nothing could be admitted.  Caller holds mu; the slot is marked busy,
+// so that its work can be enqueued without the lock (launch_batch).
+bool form_batch(saq_ingest *s, Slot &sl) {
     const int nc = (int)s->queues.size();
     // the oldest queued request decides the batch's class
     int c0 = -1;
@@ -182,7 +184,10 @@ bool dispatch(saq_ingest *s, Slot &sl) {
             c0 = c;
     if (c0 < 0) return false;
     const saq_model *m0 = s->models[(size_t)c0];
-    const bool alone = !same_class(m0, m0);  // a CUDA-core model's batch holds it alone
+    const bool alone = !groupable(m0);  // a CUDA-core model's batch holds it alone
+    // the tensor-core precision of the batch, fixed by its first model with
+    // kept dimensions (the grouped projection takes one precision)
+    int prec = m0->dk > 0 && !alone ? m0->tc.precision : -1;
     const size_t avail = s->p.hbm_budget_bytes > s->in_flight ? s->p.hbm_budget_bytes - s->in_flight : 0;
     const int64_t cap = s->p.max_batch_rows;
     std::vector<int> gidx((size_t)nc, -1);  // collection -> its group in the batch
@@ -193,7 +198,10 @@ bool dispatch(saq_ingest *s, Slot &sl) {
         int c = -1;
         for (int k = 0; k < nc; ++k) {
             if (s->queues[(size_t)k].empty()) continue;
-            if (alone ? k != c0 : !same_class(m0, s->models[(size_t)k])) continue;
+            const saq_model *mk = s->models[(size_t)k];
+            if (alone ? k != c0
+                      : !groupable(mk) || (mk->dk > 0 && prec >= 0 && mk->tc.precision != prec))
+                continue;
             if (gidx[(size_t)k] < 0 && (int)sl.groups.size() == saq::kMaxGroups) continue;
             if (c < 0 || s->queues[(size_t)k].front()->t_submit <
                              s->queues[(size_t)c].front()->t_submit)
@@ -220,6 +228,7 @@ bool dispatch(saq_ingest *s, Slot &sl) {
         }
         if (k == 0) break;
         if (gidx[(size_t)c] < 0) {
+            if (!alone && m->dk > 0) prec = m->tc.precision;
             gidx[(size_t)c] = (int)sl.groups.size();
             Group g;
             g.coll = c;
@@ -238,6 +247,27 @@ bool dispatch(saq_ingest *s, Slot &sl) {
         s->deferred += 1;
         return false;
     }
+    sl.bytes = bytes;
+    sl.busy = true;
+    sl.finished = false;
+    sl.launch_status = SAQ_OK;
+    s->in_flight += bytes;
+    s->peak = std::max(s->peak, s->in_flight);
+    s->batches += 1;
+    if (sl.groups.size() > 1) s->mixed += 1;
+    return true;
+}
+
+// Enqueue a formed batch's work on its slot stream: device memory from the
+// pool, one copy-in per piece, the encode of all its collections, the error
+// word, one copy-out per piece, the memory back to the pool, and the
+// completion callback.  Runs WITHOUT the lock (a copy to or from pageable
+// host memory blocks the calling thread until it is done, and submit, wait
+// and poll must not wait for that); it touches only the busy slot, the
+// immutable parts of the requests and the models.  Returns false if the
+// callback could not be enqueued (the stream was synchronised instead).
+bool launch_batch(saq_ingest *s, Slot &sl) {
+    const size_t bytes = sl.bytes;
     // the batch's device memory, from the pool on the slot stream
     saq_status st = SAQ_OK;
     void *buf = nullptr;
@@ -263,13 +293,6 @@ bool dispatch(saq_ingest *s, Slot &sl) {
         jobs[i] = saq::EncodeJob{m, g.X, g.rows, g.codes, g.factors, g.scratch};
     }
     sl.buf = static_cast<uint8_t *>(buf);
-    sl.bytes = bytes;
-    sl.busy = true;
-    sl.finished = false;
-    s->in_flight += bytes;
-    s->peak = std::max(s->peak, s->in_flight);
-    s->batches += 1;
-    if (sl.groups.size() > 1) s->mixed += 1;
     if (st == SAQ_OK)
         for (const Piece &pc : sl.pieces) {
             const Group &g = sl.groups[(size_t)pc.group];
@@ -294,11 +317,9 @@ bool dispatch(saq_ingest *s, Slot &sl) {
                                          cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
                          cudaMemsetAsync(sl.err_dev, 0, sizeof(int), sl.stream) != cudaSuccess))
         st = SAQ_ERR_CUDA;
+    sl.launch_status = st;  // applied to the requests at completion, under the lock
     for (const Piece &pc : sl.pieces) {
-        if (st != SAQ_OK) {
-            pc.req->status = st;
-            continue;
-        }
+        if (st != SAQ_OK) break;
         const Group &g = sl.groups[(size_t)pc.group];
         const saq_model *m = s->models[(size_t)g.coll];
         const size_t cb = m->code_bytes;
@@ -313,9 +334,9 @@ bool dispatch(saq_ingest *s, Slot &sl) {
     auto *arg = new std::pair<saq_ingest *, Slot *>(s, &sl);
     if (cudaLaunchHostFunc(sl.stream, on_batch_done, arg) != cudaSuccess) {
         delete arg;
-        for (const Piece &pc : sl.pieces) pc.req->status = SAQ_ERR_CUDA;
+        sl.launch_status = SAQ_ERR_CUDA;
         cudaStreamSynchronize(sl.stream);
-        sl.finished = true;
+        return false;
     }
     return true;
 }
@@ -327,7 +348,11 @@ void scheduler(saq_ingest *s) {
         reap(s);
         for (Slot &sl : s->slots) {
             if (sl.busy) continue;
-            if (!dispatch(s, sl)) break;  // nothing queued, or no budget left
+            if (!form_batch(s, sl)) break;  // nothing queued, or no budget left
+            lk.unlock();
+            const bool cb = launch_batch(s, sl);
+            lk.lock();
+            if (!cb) sl.finished = true;
         }
         bool busy = false, queued = false, ready = false;
         for (Slot &sl : s->slots) {

@@ -52,24 +52,26 @@ def _requests(count, seed, max_rows=9000):
 
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_ingest_mix_equals_alone_in_two_launches_per_batch(collections, prec):
-    """One slot: a large request of the d = 1536 collection occupies it (about
-    2 ms of copy-in alone) while a burst of small requests of all three
-    collections queues behind it, so that the next batches take pieces of
+    """One slot: whole-batch requests of the d = 1536 collection occupy it
+    (about 3 ms each) while a burst of small requests of all three
+    collections queues behind them, so that the next batches take pieces of
     several collections in arrival order."""
     models, _ = collections
     for m in models:
         m.set_precision(prec)
     try:
         svc = P.Ingest(models, hbm_budget_bytes=8 << 30, max_batch_rows=65536, slots=1)
-        blocker = (2, synth.power_law(65536, SPECS[2][0], 0.8, seed=77).pin_memory())
-        reqs = [blocker] + _requests(40, 5)
+        # six whole-batch requests (the same rows, read-only) hold the slot
+        # for well over the time the burst takes to submit
+        blk = synth.power_law(65536, SPECS[2][0], 0.8, seed=77).pin_memory()
+        reqs = [(2, blk)] * 6 + _requests(40, 5)
         l0 = P.saq_kernel_launch_count()
         tickets = [(c, X, svc.submit(c, X)) for c, X in reqs]
         results = [(c, X) + svc.wait(t, timeout_ms=60000) for c, X, t in tickets]
         st = svc.stats()
         launches = P.saq_kernel_launch_count() - l0
         svc.close()
-        assert st["completed"] == 41 and st["submitted"] == 41
+        assert st["completed"] == 46 and st["submitted"] == 46
         assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
         # batches mix collections, and each batch is one projection launch
         # plus one quantize launch over all of its collections
@@ -119,6 +121,51 @@ def test_ingest_admission_by_hbm_budget(collections):
     svc.close()
 
 
+def _plain_model(d, plan, precision, seed):
+    rng = np.random.default_rng(seed)
+    dk = sum(l for _, l, b in plan if b > 0)
+    Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+    mean = rng.standard_normal(d) * 0.05
+    return P.saq_model_create(d, mean, Q[:dk].copy() if dk else np.zeros((0, d)), plan,
+                              rounds=6, precision=precision)
+
+
+def test_ingest_projection_kinds_share_batches_only_when_compatible():
+    """Collections of different projection kinds in one service: FP32 split
+    and FP8 tensor-core models, a CUDA-core model (fp32_simt) and a model
+    whose plan drops every segment (only |x - c|^2 is stored).  Rows of
+    different tensor-core precisions or of the CUDA-core model never share a
+    launch; a model without kept dimensions joins any batch.  Every request
+    still equals saq_encode of its rows alone."""
+    torch.cuda.set_device(0)
+    models = [_plain_model(128, [(0, 64, 5), (64, 64, 3)], "fp32", 1),
+              _plain_model(256, [(0, 128, 4), (128, 128, 2)], "fp8", 2),
+              _plain_model(96, [(0, 64, 4), (64, 32, 2)], "fp32_simt", 3),
+              _plain_model(64, [(0, 64, 0)], "fp32", 4),
+              _plain_model(192, [(0, 64, 8), (64, 128, 1)], "fp8", 5)]
+    assert [m.tensor_cores for m in models] == [True, True, False, False, True]
+    assert models[3].d_kept == 0 and models[3].code_bytes == 0
+    dims = [m.d for m in models]
+    svc = P.Ingest(models, hbm_budget_bytes=4 << 30, max_batch_rows=65536, slots=1)
+    rng = np.random.default_rng(8)
+    blocker = synth.power_law(65536, 256, 0.8, seed=55).pin_memory()
+    reqs = [(1, blocker)] * 16
+    for i in range(60):
+        c = int(rng.integers(0, len(models)))
+        n = int(np.exp(rng.uniform(0, np.log(3000))))
+        reqs.append((c, synth.power_law(n, dims[c], 0.8, seed=700 + i).pin_memory()))
+    tickets = [(c, X, svc.submit(c, X)) for c, X in reqs]
+    results = [(c, X) + svc.wait(t, timeout_ms=60000) for c, X, t in tickets]
+    st = svc.stats()
+    svc.close()
+    assert st["completed"] == len(reqs)
+    assert st["mixed_batches"] >= 1
+    for c, X, codes, factors, _ in results:
+        rc, rf = models[c].encode(X.cuda())
+        assert np.array_equal(codes.numpy()[:, :models[c].code_bytes], rc.cpu().numpy())
+        assert np.array_equal(factors.numpy(), rf.cpu().numpy())
+
+
 def test_served_rows_against_the_oracle(collections):
     """A seeded sample of the rows served in a mixed run, per collection,
     against the FP64 oracle: FP32 strict parity (every mismatch traced to an
@@ -130,10 +177,12 @@ def test_served_rows_against_the_oracle(collections):
         for m in models:
             m.set_precision(prec)
         svc = P.Ingest(models, hbm_budget_bytes=8 << 30, max_batch_rows=65536, slots=1)
-        blocker = svc.submit(2, synth.power_law(65536, SPECS[2][0], 0.8, seed=78).pin_memory())
+        blk = synth.power_law(65536, SPECS[2][0], 0.8, seed=78).pin_memory()
+        blockers = [svc.submit(2, blk) for _ in range(6)]
         tickets = [(c, X, svc.submit(c, X)) for c, X in reqs]
         got = [(c, X) + svc.wait(t, timeout_ms=60000)[:2] for c, X, t in tickets]
-        svc.wait(blocker, timeout_ms=60000)
+        for t in blockers:
+            svc.wait(t, timeout_ms=60000)
         assert svc.stats()["mixed_batches"] >= 1
         svc.close()
         rng = np.random.default_rng(3)
