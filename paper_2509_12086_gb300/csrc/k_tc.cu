@@ -19,13 +19,14 @@
 //               shared memory, converts them into the A operand(s) and
 //               accumulates |x - c|^2; after the K loop each warp drains its
 //               TMEM lane quadrant for alternate 32-column blocks with
-//               tcgen05.ld.  The split form writes its A tiles to shared
-//               memory (UMMA K-major, 64-byte rows, 64-byte swizzle); the BF16
-//               and FP8 forms write each row's A values to TMEM with
-//               tcgen05.st (one 16-column buffer per stage beside the
-//               accumulator) and their MMAs read A from there, which takes
-//               the A tile's write and its reads by the MMAs off the shared
-//               memory ports.
+//               tcgen05.ld.  Every form writes each row's A values to TMEM
+//               with tcgen05.st (16-column buffers per stage beside the
+//               accumulators: one for BF16 / FP8, a hi and a lo buffer for
+//               the split) and the MMAs read A from there, which takes the A
+//               tiles' writes and their reads by the MMAs off the shared
+//               memory ports: the split form was bound by shared-memory
+//               bandwidth (per K block the TMA, the converters and the MMAs
+//               moved 147 KB through it, 1,150 cycles at 128 B per clock).
 // Operand rows are 64 bytes per stage (32 FP16/BF16 or 64 E4M3 values), so
 // three or more stages fit in shared memory.
 // Precision modes:
@@ -66,6 +67,9 @@ enum Mode { kSplit = 0, kBF16 = 1, kFP8 = 2 };
 
 constexpr int kBM = 128;            // rows per tile (UMMA M)
 constexpr int kNPMax = 256;         // output columns per tile at most (UMMA N)
+// the split form's column passes: two accumulators of at most 192 columns
+// and four hi/lo A buffers of 32 columns share the 512 TMEM columns
+constexpr int kSplitNP = 192;
 constexpr int kPrefetch = 8;        // X boxes are prefetched into L2 this many K blocks ahead
 constexpr int kAcc2 = 256;          // TMEM column of the split mode's correction accumulator
 constexpr int kConvWarps = 8;
@@ -74,35 +78,41 @@ constexpr int kConvWarps = 8;
 constexpr int kErrRange = 16;
 constexpr int kThreads = 64 + 32 * kConvWarps;
 constexpr uint32_t kXBox = 16384;   // 128 rows x 128 bytes of staged FP32
-constexpr uint32_t kATile = 8192;   // 128 rows x 64 bytes
 constexpr uint32_t kBTile = 16384;  // 256 rows x 64 bytes
 
-// Per stage: XBOX staged X boxes, NA A-operand tiles in shared memory (0: the
-// A operand of the stage lives in TMEM), NB W-operand tiles.
+// Per stage: XBOX staged X boxes and NB W-operand tiles in shared memory (the
+// A operand of the stage lives in TMEM).
 template <int MODE> struct Cfg;
-template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage, A hi/lo in shared memory
-    static constexpr int BK = 32, STAGES = 3, NA = 2, NB = 2, XBOX = 1, TMEM = 512;
+template <> struct Cfg<kSplit> {  // 32 FP16 per row per stage, A hi/lo in TMEM
+    static constexpr int BK = 32, STAGES = 4, NB = 2, XBOX = 1, TMEM = 512;
 };
 template <> struct Cfg<kBF16> {  // 32 BF16 per row per stage, A in TMEM
-    static constexpr int BK = 32, STAGES = 6, NA = 0, NB = 1, XBOX = 1, TMEM = 512;
+    static constexpr int BK = 32, STAGES = 6, NB = 1, XBOX = 1, TMEM = 512;
 };
 template <> struct Cfg<kFP8> {  // 64 E4M3 per row per stage, A in TMEM
-    static constexpr int BK = 64, STAGES = 4, NA = 0, NB = 1, XBOX = 2, TMEM = 512;
+    static constexpr int BK = 64, STAGES = 4, NB = 1, XBOX = 2, TMEM = 512;
 };
-// TMEM column of the first A buffer of the forms that keep A in TMEM: one
-// buffer of 16 columns (64 bytes of a row) per stage, after the accumulator
+// TMEM column of the A buffers (16 columns, 64 bytes of a row, each):
+// BF16 / FP8 one per stage after the accumulator (columns 256 ..); the split
+// form a hi (part 0) and a lo (part 1) buffer per stage in the gaps beside
+// its accumulators (main 0 .. 191, correction 256 .. 447): stages 0-1 at
+// 192 .., stages 2-3 at 448 ..
 constexpr uint32_t kTA = 256;
 static_assert(kTA + 16u * Cfg<kBF16>::STAGES <= 512u && kTA + 16u * Cfg<kFP8>::STAGES <= 512u,
               "A buffers exceed the TMEM allocation");
+static_assert(Cfg<kSplit>::STAGES == 4 && kSplitNP <= 192 && kAcc2 == 256 &&
+                  kAcc2 + kSplitNP <= 448,
+              "split-form TMEM map: accumulators and A buffers overlap");
+template <int MODE> __host__ __device__ constexpr uint32_t ta_col(int s, int part) {
+    return MODE == kSplit ? (s < 2 ? 192u + 32u * (uint32_t)s : 448u + 32u * (uint32_t)(s - 2)) +
+                                16u * (uint32_t)part
+                          : kTA + 16u * (uint32_t)s;
+}
 
 template <int MODE> constexpr uint32_t stage_bytes() {
-    return (uint32_t)Cfg<MODE>::XBOX * kXBox + (uint32_t)Cfg<MODE>::NA * kATile +
-           (uint32_t)Cfg<MODE>::NB * kBTile;
+    return (uint32_t)Cfg<MODE>::XBOX * kXBox + (uint32_t)Cfg<MODE>::NB * kBTile;
 }
-template <int MODE> constexpr uint32_t a_offset() { return (uint32_t)Cfg<MODE>::XBOX * kXBox; }
-template <int MODE> constexpr uint32_t b_offset() {
-    return a_offset<MODE>() + (uint32_t)Cfg<MODE>::NA * kATile;
-}
+template <int MODE> constexpr uint32_t b_offset() { return (uint32_t)Cfg<MODE>::XBOX * kXBox; }
 // A CTA that allocates all 512 TMEM columns must be alone on its SM (an
 // allocation beyond the free columns waits for a co-resident CTA to free
 // its own): its stages alone take more than half of the 228 KB of an SM.
@@ -232,22 +242,8 @@ template <int MODE> __host__ __device__ constexpr uint32_t umma_idesc_base() {
     d |= (uint32_t)(kBM >> 4) << 24;
     return d;
 }
-template <int MODE>
-__device__ __forceinline__ void umma(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc,
-                                     uint32_t acc) {
-    if (MODE == kFP8) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    }
-}
-// the same with the A operand in TMEM (column address `atm`, 128 lanes)
+// tcgen05.mma with the A operand in TMEM (column address `atm`, 128 lanes),
+// B from shared memory (descriptor b), D in TMEM at dtm
 template <int MODE>
 __device__ __forceinline__ void umma_ta(uint32_t dtm, uint32_t atm, uint64_t b, uint32_t idesc,
                                         uint32_t acc) {
@@ -320,13 +316,10 @@ __device__ __forceinline__ uint32_t pack_b2(__nv_bfloat162 h) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// 16-byte chunk `c` of row `r`: staged FP32 (128-byte rows, 128-byte swizzle)
-// and operand tiles (64-byte rows, 64-byte swizzle).
+// 16-byte chunk `c` of row `r` of a staged FP32 box (128-byte rows, 128-byte
+// swizzle).
 __device__ __forceinline__ uint32_t swz128(int r, int c) {
     return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
-}
-__device__ __forceinline__ uint32_t swz64(int r, int c) {
-    return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
 // The work of one CTA: row tile `tile`, column pass `pass` of one model
@@ -426,22 +419,18 @@ __device__ __forceinline__ void proj_tile(
                 if (!mbar_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) break;
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + s * SB);
-                const uint64_t a0 = umma_desc(st + a_offset<MODE>());
-                const uint64_t a1 = umma_desc(st + a_offset<MODE>() + kATile);
                 const uint64_t b0 = umma_desc(st + b_offset<MODE>());
                 const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
+                // A of the stage in TMEM, 8 columns per 32-byte K step
+                const uint32_t ahi = tmem + ta_col<MODE>(s, 0), alo = tmem + ta_col<MODE>(s, 1);
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
                     const uint64_t off = (uint64_t)(kk * 2);
-                    if (C::NA == 0) {  // A of the stage in TMEM, 8 columns per K step
-                        umma_ta<MODE>(tmem, tmem + kTA + 16u * (uint32_t)s + 8u * (uint32_t)kk,
-                                      b0 + off, idesc, (kb | kk) != 0);
-                        continue;
-                    }
-                    umma<MODE>(tmem, a0 + off, b0 + off, idesc, (kb | kk) != 0);
-                    if (C::NA == 2) {
-                        umma<MODE>(tmem + kAcc2, a0 + off, b1 + off, idesc, (kb | kk) != 0);
-                        umma<MODE>(tmem + kAcc2, a1 + off, b0 + off, idesc, 1u);
+                    const uint32_t ka = 8u * (uint32_t)kk;
+                    umma_ta<MODE>(tmem, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
+                    if (MODE == kSplit) {
+                        umma_ta<MODE>(tmem + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
+                        umma_ta<MODE>(tmem + kAcc2, alo + ka, b0 + off, idesc, 1u);
                     }
                 }
                 umma_commit(&empty[s]);
@@ -476,9 +465,9 @@ __device__ __forceinline__ void proj_tile(
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) { ok = false; break; }
             uint8_t *st = smem + s * SB;
-            uint8_t *a0 = st + a_offset<MODE>();
             const float *mk = mcs + kb * C::BK;
-            uint32_t wa[16];  // A row of the stage for the forms that keep A in TMEM
+            uint32_t wa[16];  // the row's A values of the stage (split: the hi part)
+            uint32_t wl[16];  // split: the lo part
             if (MODE == kFP8) {
                 // 4 chunks of 16 E4M3 (64 values) per thread, from the two staged boxes
 #pragma unroll
@@ -505,7 +494,6 @@ __device__ __forceinline__ void proj_tile(
                     for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 16i + 4e .. + 3
                 }
             } else {
-                uint8_t *a1 = a0 + kATile;
                 // 4 chunks of 8 values (32 values) per thread from the staged box
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -528,30 +516,23 @@ __device__ __forceinline__ void proj_tile(
 #pragma unroll
                         for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 8i + 2e, + 1
                     } else {
-                        uint32_t wh[4], wl[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
+                        for (int e = 0; e < 4; ++e) {  // values 8i + 2e, + 1
                             const __half2 hh = __floats2half2_rn(y[2 * e], y[2 * e + 1]);
                             const float2 hf = __half22float2(hh);
-                            wh[e] = pack_h2(hh);
-                            wl[e] = pack_h2(__floats2half2_rn(y[2 * e] - hf.x, y[2 * e + 1] - hf.y));
+                            wa[4 * i + e] = pack_h2(hh);
+                            wl[4 * i + e] =
+                                pack_h2(__floats2half2_rn(y[2 * e] - hf.x, y[2 * e + 1] - hf.y));
                         }
-                        *reinterpret_cast<uint4 *>(a0 + swz64(r, ac)) =
-                            make_uint4(wh[0], wh[1], wh[2], wh[3]);
-                        *reinterpret_cast<uint4 *>(a1 + swz64(r, ac)) =
-                            make_uint4(wl[0], wl[1], wl[2], wl[3]);
                     }
                 }
             }
-            if (C::NA == 0) {
-                // TMEM column c of the buffer holds the row's values of K
-                // offsets c * (4 / element bytes) upward, lowest in the low bits
-                tmem_st16(tq + kTA + 16u * (uint32_t)s, wa);
-                tmem_st_wait();
-                tc_fence_before();
-            } else {
-                fence_proxy_async();
-            }
+            // TMEM column c of a buffer holds the row's values of K offsets
+            // c * (4 / element bytes) upward, lowest in the low bits
+            tmem_st16(tq + ta_col<MODE>(s, 0), wa);
+            if (MODE == kSplit) tmem_st16(tq + ta_col<MODE>(s, 1), wl);
+            tmem_st_wait();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv[s]);
         }
@@ -593,7 +574,7 @@ __device__ __forceinline__ void proj_tile(
 #pragma unroll
                 for (int i = 0; i < 8; ++i) sc[i] = __ldg(reinterpret_cast<const float4 *>(col_scale + cb) + i);
                 float v[32];
-                if (C::NA == 2) {
+                if (MODE == kSplit) {
                     float v2[32];
                     tmem_ld32x2(tq + (uint32_t)c, tq + (uint32_t)(kAcc2 + c), v, v2);
 #pragma unroll
@@ -844,8 +825,10 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     const int BK = precision == SAQ_PREC_FP8 ? 64 : 32;
     const int dpad = (m->d + BK - 1) / BK * BK;
     const int d = m->d, dk = m->dk;
-    // balanced column passes of at most 256 columns, multiples of 16
-    const int npass = (dk + kNPMax - 1) / kNPMax;
+    // balanced column passes of at most 256 columns (split: 192), multiples
+    // of 16
+    const int npmax = precision == SAQ_PREC_FP32 ? kSplitNP : kNPMax;
+    const int npass = (dk + npmax - 1) / npmax;
     const int np = ((dk + npass - 1) / npass + 15) / 16 * 16;
     const int dkpad = npass * np;
     // input scale from the fitted variances (a power of two: exact)
