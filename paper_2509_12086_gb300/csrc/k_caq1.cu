@@ -34,6 +34,9 @@ namespace saq {
 namespace {
 
 constexpr int kU = 8;  // loads in flight per lane in every pass
+// the most dynamic shared memory a quantize block takes for its codes (at
+// least three blocks of 256 threads per SM)
+constexpr size_t kCaqSmemMax = 72 * 1024;
 constexpr int kMaxSeg = 64;
 
 struct Seg {
@@ -65,10 +68,70 @@ template <int G> struct CaqBatch {
     CaqGroup g[G];
 };
 
+// Where a lane keeps its vector-segment's codes during the adjustment.  Every
+// access is by batches of kU = 8 coordinates starting at a multiple of 8:
+//   load(j0, c, n)   the codes j0 .. j0 + n - 1 into c (0 past n)
+//   write(j0, c, n)  store a batch's codes (the initial codes)
+//   put(j, c)        code j changed by an accepted move
+//   flush(j0, c, n)  the batch's codes after its step (a changed batch)
+// GlobalCodes: one byte per coordinate in global memory, interleaved like
+// the projected rows (byte j of the lane at j * 32), written at each move.
+struct GlobalCodes {
+    uint8_t *cp;
+    static constexpr int kMinB = 1, kMaxB = 8;
+    __device__ __forceinline__ void load(int j0, int (&c)[kU], int n) const {
+        if (n >= kU) {
+#pragma unroll
+            for (int k = 0; k < kU; ++k) c[k] = (int)cp[(int64_t)(j0 + k) << 5];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kU; ++k) c[k] = k < n ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
+        }
+    }
+    __device__ __forceinline__ void write(int j0, const int (&c)[kU], int n) const {
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (k < n) cp[(int64_t)(j0 + k) << 5] = (uint8_t)c[k];
+    }
+    __device__ __forceinline__ void put(int j, int c) const { cp[(int64_t)j << 5] = (uint8_t)c; }
+    __device__ __forceinline__ void flush(int, const int (&)[kU], int) const {}
+};
+// SmemCodes<BITS>: packed in shared memory, BITS = 4 (B <= 4: one 32-bit word
+// per batch) or 8 (B <= 8: two words per batch); word w of the lane at
+// cw[w * 32] (the 32 lanes' words of one index are consecutive: no bank
+// conflict); a changed batch is stored back whole after its step.
+template <int BITS> struct SmemCodes {
+    uint32_t *cw;
+    static constexpr int kMinB = BITS == 4 ? 1 : 5, kMaxB = BITS;
+    static constexpr int kWords = BITS / 4;  // words per batch
+    __device__ __forceinline__ void load(int j0, int (&c)[kU], int) const {
+        uint32_t w[kWords];
+#pragma unroll
+        for (int i = 0; i < kWords; ++i) w[i] = cw[((j0 >> 3) * kWords + i) << 5];
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            c[k] = (int)((w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
+    }
+    __device__ __forceinline__ void write(int j0, const int (&c)[kU], int n) const {
+        uint32_t w[kWords];
+#pragma unroll
+        for (int i = 0; i < kWords; ++i) w[i] = 0u;
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            if (k < n) w[k * BITS / 32] |= (uint32_t)c[k] << ((k * BITS) & 31);
+#pragma unroll
+        for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = w[i];
+    }
+    __device__ __forceinline__ void put(int, int) const {}
+    __device__ __forceinline__ void flush(int j0, const int (&c)[kU], int n) const {
+        write(j0, c, n);
+    }
+};
+
 // Bit-planes of one lane's segment from its codes (most significant first,
 // 64-bit words); returns |u|^2 of the codes, exactly.
-template <int B>
-__device__ __forceinline__ int pack_segment(const uint8_t *cp, int len, bool valid,
+template <int B, class CS>
+__device__ __forceinline__ int pack_segment(const CS &cs, int len, bool valid,
                                             uint64_t *cout, int words) {
     constexpr int cmax = (1 << B) - 1;
     uint64_t w[B];
@@ -77,13 +140,7 @@ __device__ __forceinline__ int pack_segment(const uint8_t *cp, int len, bool val
     int S = 0;
     for (int j0 = 0; j0 < len; j0 += kU) {
         int c[kU];
-        if (j0 + kU <= len) {
-#pragma unroll
-            for (int k = 0; k < kU; ++k) c[k] = (int)cp[(int64_t)(j0 + k) << 5];
-        } else {
-#pragma unroll
-            for (int k = 0; k < kU; ++k) c[k] = j0 + k < len ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
-        }
+        cs.load(j0, c, len - j0);
         // plane p of the kU codes as the bits of one byte (past the end: 0)
 #pragma unroll
         for (int p = 0; p < B; ++p) {
@@ -146,8 +203,8 @@ __device__ __forceinline__ int caq_step(LaneState &L, float x, int c, int ubias,
 // its own step is done, so the bit-planes (most significant first, 64-bit
 // words) and the exact |u|^2, which the function returns, are built as the
 // round goes.
-template <int PACK_B>
-__device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t *cp, int len,
+template <int PACK_B, class CS>
+__device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS &cs, int len,
                                          int cmax, bool &moved, bool valid, uint64_t *cout,
                                          int words) {
     const int ubias = 0x4B400000 - cmax;
@@ -162,7 +219,7 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t 
         bool accepted = false;
         c = caq_step(L, x, c, ubias, cmaxf, accepted);
         if (accepted) {
-            cp[(int64_t)j << 5] = (uint8_t)c;
+            cs.put(j, c);
             moved = true;
         }
         return c;
@@ -195,30 +252,32 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t 
     float xb[kU];
     int cb[kU];
 #pragma unroll
-    for (int k = 0; k < kU; ++k) {
-        xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
-        cb[k] = k < len ? (int)cp[(int64_t)k << 5] : 0;
-    }
+    for (int k = 0; k < kU; ++k) xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
+    cs.load(0, cb, len);
     for (int j0 = 0; j0 < lenU; j0 += kU) {
         float xn[kU];
         int cn[kU];
         if (j0 + 2 * kU <= len) {  // the next batch lies inside the segment
 #pragma unroll
-            for (int k = 0; k < kU; ++k) {
-                xn[k] = __ldg(op + ((int64_t)(j0 + kU + k) << 5));
-                cn[k] = (int)cp[(int64_t)(j0 + kU + k) << 5];
-            }
+            for (int k = 0; k < kU; ++k) xn[k] = __ldg(op + ((int64_t)(j0 + kU + k) << 5));
         } else {
 #pragma unroll
             for (int k = 0; k < kU; ++k) {
                 const int jn = j0 + kU + k;
                 xn[k] = jn < len ? __ldg(op + ((int64_t)jn << 5)) : 0.f;
-                cn[k] = jn < len ? (int)cp[(int64_t)jn << 5] : 0;
             }
         }
+        // the next batch's codes (a code is written at its own step, and a
+        // batch is stored back after its steps: the next one is current)
+        if (j0 + kU < len) cs.load(j0 + kU, cn, len - j0 - kU);
         int cf[kU];
+        bool changed = false;
 #pragma unroll
-        for (int k = 0; k < kU; ++k) cf[k] = step(xb[k], cb[k], j0 + k);
+        for (int k = 0; k < kU; ++k) {
+            cf[k] = step(xb[k], cb[k], j0 + k);
+            changed |= cf[k] != cb[k];
+        }
+        if (changed) cs.flush(j0, cf, kU);
         pack(cf, j0, kU);
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
@@ -229,40 +288,49 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, uint8_t 
     // the last, partial batch
     if (lenU < len) {
         int cf[kU];
+        bool changed = false;
 #pragma unroll
-        for (int k = 0; k < kU; ++k) cf[k] = lenU + k < len ? step(xb[k], cb[k], lenU + k) : 0;
+        for (int k = 0; k < kU; ++k) {
+            cf[k] = lenU + k < len ? step(xb[k], cb[k], lenU + k) : 0;
+            changed |= cf[k] != cb[k];
+        }
+        if (changed) cs.flush(lenU, cf, len - lenU);
         pack(cf, lenU, len - lenU);
     }
     return Si;
 }
 
-// The work of warp w of one model's launch: one warp per (kept segment,
-// group of 32 rows).
-__device__ __forceinline__ void caq1_warp(int64_t w, const float *__restrict__ Oi, int64_t n,
-                                          int dk, int nseg, const SegTable &t, int rounds,
-                                          uint8_t *__restrict__ cs,
-                                          const float *__restrict__ vmax_arr,
-                                          uint8_t *__restrict__ codes, int64_t code_stride,
-                                          float *__restrict__ factors, int nf) {
-    const int lane = threadIdx.x & 31;
-    const int64_t groups = (n + 31) / 32;
-    const int si = t.order[w / groups];
-    const Seg sg = t.s[si];
-    const int64_t g = w % groups;
-    const int off = sg.off, len = sg.len, B = sg.bits, words = sg.words, fidx = sg.fidx;
-    const long long code_off = sg.code_off;
-    const int cmax = (1 << B) - 1;
-    const int64_t v = g * 32 + lane;
-    const bool valid = v < n;
-    const float *op = Oi + ((g * dk + off) << 5) + lane;
-    uint8_t *cp = cs + ((g * dk + off) << 5) + lane;
+// The last round (which packs as it goes) and the separate packing pass for
+// B bits, instantiated only for the bit widths the code store holds.
+template <int B, class CS>
+__device__ __forceinline__ int last_round(LaneState &L, const float *op, const CS &cs, int len,
+                                          int cmax, bool &moved, bool valid, uint64_t *cout,
+                                          int words) {
+    if constexpr (B >= CS::kMinB && B <= CS::kMaxB)
+        return run_round<B, CS>(L, op, cs, len, cmax, moved, valid, cout, words);
+    else
+        return 0;
+}
+template <int B, class CS>
+__device__ __forceinline__ int pack_only(const CS &cs, int len, bool valid, uint64_t *cout,
+                                         int words) {
+    if constexpr (B >= CS::kMinB && B <= CS::kMaxB)
+        return pack_segment<B, CS>(cs, len, valid, cout, words);
+    else
+        return 0;
+}
 
-    // v_max of the lane's vector-segment, recorded by the projection
-    const float vmax = valid ? __ldg(vmax_arr + ((g * nseg + si) << 5) + lane) : 0.f;
+// Algorithm 1 on one lane's vector-segment with its codes in store cs:
+// initial codes, the rounds, the packing and the two factors.
+template <class CS>
+__device__ __forceinline__ void caq_segment(const CS &cs, const float *op, int len, int B,
+                                            int words, bool valid, float vmax, int rounds,
+                                            uint64_t *cout, float *fo) {
+    const int cmax = (1 << B) - 1;
     const bool live = valid && vmax > 0.f;
     // initial codes, Eq. find_nearest_code: c = floor((o + v_max) / Delta),
     // Delta = 2 v_max / 2^B; with I = <u, o>, S = |u|^2 and |o|^2
-    // (in FP32: the code c as a float, clamped, its byte from the bits of
+    // (in FP32: the code c as a float, clamped, the integer from the bits of
     // c + 2^23; |u|^2 is summed in FP32 for the decisions and recounted
     // exactly while packing).  Every lane of the last group of 32 rows reads
     // rows the buffer holds; a lane past n keeps codes 0.
@@ -270,70 +338,114 @@ __device__ __forceinline__ void caq1_warp(int64_t w, const float *__restrict__ O
     const float off_c = vmax * inv_delta;  // (o + v_max) / Delta = o / Delta + off_c
     const float cmaxf = (float)cmax;
     float I = 0.f, n2 = 0.f, S = 0.f;
-    auto init = [&](float x, int j) {
+    auto init = [&](float x) {
         const float cf = fminf(fmaxf(floorf(fmaf(x, inv_delta, off_c)), 0.f), cmaxf);
-        cp[(int64_t)j << 5] = (uint8_t)__float_as_uint(cf + 8388608.f);
         const float u = fmaf(2.f, cf, -cmaxf);
         I = fmaf(u, x, I);
         n2 = fmaf(x, x, n2);
         S = fmaf(u, u, S);
+        return (int)(__float_as_uint(cf + 8388608.f) & 0xFFu);
     };
     const int lenU = len & ~(kU - 1);  // coordinates in whole batches
     for (int j0 = 0; j0 < lenU; j0 += kU) {
         float x[kU];
 #pragma unroll
         for (int k = 0; k < kU; ++k) x[k] = __ldg(op + ((int64_t)(j0 + k) << 5));
+        int c[kU];
 #pragma unroll
-        for (int k = 0; k < kU; ++k) init(live ? x[k] : 0.f, j0 + k);
+        for (int k = 0; k < kU; ++k) c[k] = init(live ? x[k] : 0.f);
+        cs.write(j0, c, kU);
     }
-    for (int j = lenU; j < len; ++j) init(live ? __ldg(op + ((int64_t)j << 5)) : 0.f, j);
+    if (lenU < len) {
+        int c[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k)
+            c[k] = lenU + k < len ? init(live ? __ldg(op + ((int64_t)(lenU + k) << 5)) : 0.f) : 0;
+        cs.write(lenU, c, len - lenU);
+    }
     LaneState L{I, S, live ? I * I : __int_as_float(0x7f800000)};
-    uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
     int Si = -1;  // |u|^2 of the final codes, exactly, once they are packed
     for (int r = 0; r < rounds; ++r) {
         if (!__any_sync(0xffffffffu, L.I2 != __int_as_float(0x7f800000))) break;
         bool moved = false;
         if (r == rounds - 1) {  // the last round packs as it goes
             switch (B) {  // uniform per warp
-                case 1: Si = run_round<1>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                case 2: Si = run_round<2>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                case 3: Si = run_round<3>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                case 4: Si = run_round<4>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                case 5: Si = run_round<5>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                case 6: Si = run_round<6>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                case 7: Si = run_round<7>(L, op, cp, len, cmax, moved, valid, cout, words); break;
-                default: Si = run_round<8>(L, op, cp, len, cmax, moved, valid, cout, words); break;
+                case 1: Si = last_round<1, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                case 2: Si = last_round<2, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                case 3: Si = last_round<3, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                case 4: Si = last_round<4, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                case 5: Si = last_round<5, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                case 6: Si = last_round<6, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                case 7: Si = last_round<7, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
+                default: Si = last_round<8, CS>(L, op, cs, len, cmax, moved, valid, cout, words); break;
             }
             break;
         }
-        run_round<0>(L, op, cp, len, cmax, moved, valid, cout, words);
+        run_round<0, CS>(L, op, cs, len, cmax, moved, valid, cout, words);
         if (!moved) L.I2 = __int_as_float(0x7f800000);
     }
     I = L.I;
     // every lane done before the last round (or no rounds): pack from the codes
     if (Si < 0) {
         switch (B) {  // uniform per warp
-            case 1: Si = pack_segment<1>(cp, len, valid, cout, words); break;
-            case 2: Si = pack_segment<2>(cp, len, valid, cout, words); break;
-            case 3: Si = pack_segment<3>(cp, len, valid, cout, words); break;
-            case 4: Si = pack_segment<4>(cp, len, valid, cout, words); break;
-            case 5: Si = pack_segment<5>(cp, len, valid, cout, words); break;
-            case 6: Si = pack_segment<6>(cp, len, valid, cout, words); break;
-            case 7: Si = pack_segment<7>(cp, len, valid, cout, words); break;
-            default: Si = pack_segment<8>(cp, len, valid, cout, words); break;
+            case 1: Si = pack_only<1, CS>(cs, len, valid, cout, words); break;
+            case 2: Si = pack_only<2, CS>(cs, len, valid, cout, words); break;
+            case 3: Si = pack_only<3, CS>(cs, len, valid, cout, words); break;
+            case 4: Si = pack_only<4, CS>(cs, len, valid, cout, words); break;
+            case 5: Si = pack_only<5, CS>(cs, len, valid, cout, words); break;
+            case 6: Si = pack_only<6, CS>(cs, len, valid, cout, words); break;
+            case 7: Si = pack_only<7, CS>(cs, len, valid, cout, words); break;
+            default: Si = pack_only<8, CS>(cs, len, valid, cout, words); break;
         }
     }
     if (valid) {
-        float *fo = factors + v * nf;
         if (live) {
             const float nrm = sqrtf(n2);
-            fo[fidx] = nrm;
-            fo[fidx + 1] = I / (sqrtf((float)Si) * nrm);
+            fo[0] = nrm;
+            fo[1] = I / (sqrtf((float)Si) * nrm);
         } else {
             // all-zero segment (the paper is silent): codes 0, |o| = 0, cos = 1
-            fo[fidx] = 0.f;
-            fo[fidx + 1] = 1.f;
+            fo[0] = 0.f;
+            fo[1] = 1.f;
         }
+    }
+}
+
+// The work of warp w of one model's launch: one warp per (kept segment,
+// group of 32 rows).  SMEM_CODES: the codes live in the warp's region of
+// the block's shared memory (words_per_lane 32-bit words per lane), else in
+// the byte scratch cs.
+template <bool SMEM_CODES>
+__device__ __forceinline__ void caq1_warp(int64_t w, const float *__restrict__ Oi, int64_t n,
+                                          int dk, int nseg, const SegTable &t, int rounds,
+                                          uint8_t *__restrict__ cs,
+                                          const float *__restrict__ vmax_arr,
+                                          uint8_t *__restrict__ codes, int64_t code_stride,
+                                          float *__restrict__ factors, int nf,
+                                          uint32_t *smem_codes, int words_per_lane) {
+    const int lane = threadIdx.x & 31;
+    const int64_t groups = (n + 31) / 32;
+    const int si = t.order[w / groups];
+    const Seg sg = t.s[si];
+    const int64_t g = w % groups;
+    const int off = sg.off, len = sg.len, B = sg.bits, words = sg.words, fidx = sg.fidx;
+    const long long code_off = sg.code_off;
+    const int64_t v = g * 32 + lane;
+    const bool valid = v < n;
+    const float *op = Oi + ((g * dk + off) << 5) + lane;
+    // v_max of the lane's vector-segment, recorded by the projection
+    const float vmax = valid ? __ldg(vmax_arr + ((g * nseg + si) << 5) + lane) : 0.f;
+    uint64_t *cout = reinterpret_cast<uint64_t *>(codes + v * code_stride + code_off);
+    float *fo = factors + v * nf + fidx;
+    if constexpr (SMEM_CODES) {
+        uint32_t *cw = smem_codes + (threadIdx.x >> 5) * (words_per_lane << 5) + lane;
+        if (B <= 4)  // uniform per warp
+            caq_segment(SmemCodes<4>{cw}, op, len, B, words, valid, vmax, rounds, cout, fo);
+        else
+            caq_segment(SmemCodes<8>{cw}, op, len, B, words, valid, vmax, rounds, cout, fo);
+    } else {
+        caq_segment(GlobalCodes{cs + ((g * dk + off) << 5) + lane}, op, len, B, words, valid, vmax,
+                    rounds, cout, fo);
     }
 }
 
@@ -346,7 +458,22 @@ k_caq1(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable
        uint8_t *__restrict__ codes, int64_t code_stride, float *__restrict__ factors, int nf) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= (n + 31) / 32 * nseg) return;  // uniform per warp
-    caq1_warp(w, Oi, n, dk, nseg, t, rounds, cs, vmax_arr, codes, code_stride, factors, nf);
+    caq1_warp<false>(w, Oi, n, dk, nseg, t, rounds, cs, vmax_arr, codes, code_stride, factors, nf,
+                     nullptr, 0);
+}
+
+// The same with every warp's codes in shared memory (words_per_lane 32-bit
+// words per lane: 4-bit codes for B <= 4, bytes above): the adjustment
+// rounds then read only the projected rows from global memory.
+__global__ void __launch_bounds__(256, 4)
+k_caq1_sm(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTable t, int rounds,
+          const float *__restrict__ vmax_arr, uint8_t *__restrict__ codes, int64_t code_stride,
+          float *__restrict__ factors, int nf, int words_per_lane) {
+    extern __shared__ uint32_t smem_codes[];
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (n + 31) / 32 * nseg) return;  // uniform per warp
+    caq1_warp<true>(w, Oi, n, dk, nseg, t, rounds, nullptr, vmax_arr, codes, code_stride, factors,
+                    nf, smem_codes, words_per_lane);
 }
 
 // The rows of up to kMaxGroups models (a batch of several collections) in
@@ -359,8 +486,8 @@ k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch) {
     while (gi + 1 < batch.ngroups && wg >= batch.warp_start[gi + 1]) ++gi;
     if (wg >= batch.warp_start[batch.ngroups]) return;  // uniform per warp
     const CaqGroup &P = batch.g[gi];
-    caq1_warp(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds, P.cs, P.vmax,
-              P.codes, P.code_stride, P.factors, P.nf);
+    caq1_warp<false>(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds, P.cs,
+                     P.vmax, P.codes, P.code_stride, P.factors, P.nf, nullptr, 0);
 }
 
 // The instruction ceiling of the adjustment: caq_step on coordinates held in
@@ -470,10 +597,28 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
     if (st != SAQ_OK) return st;
     const int64_t warps = (n + 31) / 32 * g.nseg;
     const int64_t blocks = (warps + 7) / 8;
+    // codes in shared memory when a block of 8 warps needs at most 72 KB
+    // (at least 3 blocks per SM); otherwise in the global byte scratch
+    int wpl = 0;  // 32-bit words per lane: one per 8 coordinates (4-bit codes) or two (bytes)
+    for (const KeptSeg &k : m->kept) wpl = std::max(wpl, (k.len + 7) / 8 * (k.bits <= 4 ? 1 : 2));
+    const size_t smem = (size_t)wpl * 32 * 4 * 8;
     {
         LaunchTimer lt_(kKindQuantize, s);
-        k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, g.dk, g.nseg, g.t, g.rounds, cs, vmax,
-                                                codes, g.code_stride, factors, g.nf);
+        if (smem <= kCaqSmemMax) {
+            SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_caq1_sm,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)kCaqSmemMax));
+            // all of the unified L1 / shared storage as shared memory: four
+            // blocks of 56 KB fit (the d = 960 plan's longest segment)
+            SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_caq1_sm,
+                                                cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                100));
+            k_caq1_sm<<<(unsigned)blocks, 256, smem, s>>>(Oi, n, g.dk, g.nseg, g.t, g.rounds, vmax,
+                                                          codes, g.code_stride, factors, g.nf, wpl);
+        } else {
+            k_caq1<<<(unsigned)blocks, 256, 0, s>>>(Oi, n, g.dk, g.nseg, g.t, g.rounds, cs, vmax,
+                                                    codes, g.code_stride, factors, g.nf);
+        }
     }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
