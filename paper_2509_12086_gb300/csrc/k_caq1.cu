@@ -69,17 +69,19 @@ template <int G> struct CaqBatch {
 };
 
 // Where a lane keeps its vector-segment's codes during the adjustment.  Every
-// access is by batches of kU = 8 coordinates starting at a multiple of 8:
-//   load(j0, c, n)   the codes j0 .. j0 + n - 1 into c (0 past n)
-//   write(j0, c, n)  store a batch's codes (the initial codes)
-//   put(j, c)        code j changed by an accepted move
-//   flush(j0, c, n)  the batch's codes after its step (a changed batch)
+// access is by batches of kU = 8 coordinates starting at a multiple of 8,
+// through a batch state held in registers:
+//   load(j0, bt, c, n)   the codes j0 .. j0 + n - 1 into c (0 past n)
+//   put(bt, j0, k, c)    code j0 + k changed by an accepted move
+//   flush(bt, j0)        after the batch's steps
+//   write(j0, c, n)      store a batch's codes (the initial codes)
 // GlobalCodes: one byte per coordinate in global memory, interleaved like
 // the projected rows (byte j of the lane at j * 32), written at each move.
 struct GlobalCodes {
     uint8_t *cp;
     static constexpr int kMinB = 1, kMaxB = 8;
-    __device__ __forceinline__ void load(int j0, int (&c)[kU], int n) const {
+    struct Batch {};
+    __device__ __forceinline__ void load(int j0, Batch &, int (&c)[kU], int n) const {
         if (n >= kU) {
 #pragma unroll
             for (int k = 0; k < kU; ++k) c[k] = (int)cp[(int64_t)(j0 + k) << 5];
@@ -93,24 +95,31 @@ struct GlobalCodes {
         for (int k = 0; k < kU; ++k)
             if (k < n) cp[(int64_t)(j0 + k) << 5] = (uint8_t)c[k];
     }
-    __device__ __forceinline__ void put(int j, int c) const { cp[(int64_t)j << 5] = (uint8_t)c; }
-    __device__ __forceinline__ void flush(int, const int (&)[kU], int) const {}
+    __device__ __forceinline__ void put(Batch &, int j0, int k, int c) const {
+        cp[(int64_t)(j0 + k) << 5] = (uint8_t)c;
+    }
+    __device__ __forceinline__ void flush(Batch &, int) const {}
 };
 // SmemCodes<BITS>: packed in shared memory, BITS = 4 (B <= 4: one 32-bit word
 // per batch) or 8 (B <= 8: two words per batch); word w of the lane at
 // cw[w * 32] (the 32 lanes' words of one index are consecutive: no bank
-// conflict); a changed batch is stored back whole after its step.
+// conflict).  A move inserts its code into the batch's word in a register;
+// a batch with a move is stored back once, after its steps.
 template <int BITS> struct SmemCodes {
     uint32_t *cw;
     static constexpr int kMinB = BITS == 4 ? 1 : 5, kMaxB = BITS;
     static constexpr int kWords = BITS / 4;  // words per batch
-    __device__ __forceinline__ void load(int j0, int (&c)[kU], int) const {
+    struct Batch {
         uint32_t w[kWords];
+        bool dirty;
+    };
+    __device__ __forceinline__ void load(int j0, Batch &bt, int (&c)[kU], int) const {
 #pragma unroll
-        for (int i = 0; i < kWords; ++i) w[i] = cw[((j0 >> 3) * kWords + i) << 5];
+        for (int i = 0; i < kWords; ++i) bt.w[i] = cw[((j0 >> 3) * kWords + i) << 5];
+        bt.dirty = false;
 #pragma unroll
         for (int k = 0; k < kU; ++k)
-            c[k] = (int)((w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
+            c[k] = (int)((bt.w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
     }
     __device__ __forceinline__ void write(int j0, const int (&c)[kU], int n) const {
         uint32_t w[kWords];
@@ -122,9 +131,18 @@ template <int BITS> struct SmemCodes {
 #pragma unroll
         for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = w[i];
     }
-    __device__ __forceinline__ void put(int, int) const {}
-    __device__ __forceinline__ void flush(int j0, const int (&c)[kU], int n) const {
-        write(j0, c, n);
+    __device__ __forceinline__ void put(Batch &bt, int, int k, int c) const {
+        constexpr uint32_t mask = (1u << BITS) - 1u;
+        const int sh = (k * BITS) & 31;
+        uint32_t &w = bt.w[k * BITS / 32];
+        w = (w & ~(mask << sh)) | ((uint32_t)c << sh);
+        bt.dirty = true;
+    }
+    __device__ __forceinline__ void flush(Batch &bt, int j0) const {
+        if (bt.dirty) {
+#pragma unroll
+            for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = bt.w[i];
+        }
     }
 };
 
@@ -140,7 +158,8 @@ __device__ __forceinline__ int pack_segment(const CS &cs, int len, bool valid,
     int S = 0;
     for (int j0 = 0; j0 < len; j0 += kU) {
         int c[kU];
-        cs.load(j0, c, len - j0);
+        typename CS::Batch bt;
+        cs.load(j0, bt, c, len - j0);
         // plane p of the kU codes as the bits of one byte (past the end: 0)
 #pragma unroll
         for (int p = 0; p < B; ++p) {
@@ -215,11 +234,12 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
 #pragma unroll
     for (int p = 0; p < NW; ++p) w[p] = 0ull;
     int Si = 0;
-    auto step = [&](float x, int c, int j) {
+    typename CS::Batch bb, bn;  // the current and the next batch's code state
+    auto step = [&](float x, int c, int j0, int k) {
         bool accepted = false;
         c = caq_step(L, x, c, ubias, cmaxf, accepted);
         if (accepted) {
-            cs.put(j, c);
+            cs.put(bb, j0, k, c);
             moved = true;
         }
         return c;
@@ -253,7 +273,7 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
     int cb[kU];
 #pragma unroll
     for (int k = 0; k < kU; ++k) xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
-    cs.load(0, cb, len);
+    cs.load(0, bb, cb, len);
     for (int j0 = 0; j0 < lenU; j0 += kU) {
         float xn[kU];
         int cn[kU];
@@ -269,16 +289,13 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
         }
         // the next batch's codes (a code is written at its own step, and a
         // batch is stored back after its steps: the next one is current)
-        if (j0 + kU < len) cs.load(j0 + kU, cn, len - j0 - kU);
+        if (j0 + kU < len) cs.load(j0 + kU, bn, cn, len - j0 - kU);
         int cf[kU];
-        bool changed = false;
 #pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            cf[k] = step(xb[k], cb[k], j0 + k);
-            changed |= cf[k] != cb[k];
-        }
-        if (changed) cs.flush(j0, cf, kU);
+        for (int k = 0; k < kU; ++k) cf[k] = step(xb[k], cb[k], j0, k);
+        cs.flush(bb, j0);
         pack(cf, j0, kU);
+        bb = bn;
 #pragma unroll
         for (int k = 0; k < kU; ++k) {
             xb[k] = xn[k];
@@ -288,13 +305,9 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
     // the last, partial batch
     if (lenU < len) {
         int cf[kU];
-        bool changed = false;
 #pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            cf[k] = lenU + k < len ? step(xb[k], cb[k], lenU + k) : 0;
-            changed |= cf[k] != cb[k];
-        }
-        if (changed) cs.flush(lenU, cf, len - lenU);
+        for (int k = 0; k < kU; ++k) cf[k] = lenU + k < len ? step(xb[k], cb[k], lenU, k) : 0;
+        cs.flush(bb, lenU);
         pack(cf, lenU, len - lenU);
     }
     return Si;
