@@ -72,7 +72,8 @@ template <int G> struct CaqBatch {
 // access is by batches of kU = 8 coordinates starting at a multiple of 8,
 // through a batch state held in registers:
 //   load(j0, bt, c, n)   the codes j0 .. j0 + n - 1 into c (0 past n)
-//   put(bt, j0, k, c)    code j0 + k changed by an accepted move
+//   move(bt, j0, k, c, sgn)  code j0 + k (now c) moves by one, up (sgn = 0)
+//                        or down (sgn = 0x80000000), by an accepted move
 //   flush(bt, j0)        after the batch's steps
 //   write(j0, c, n)      store a batch's codes (the initial codes)
 // GlobalCodes: one byte per coordinate in global memory, interleaved like
@@ -95,28 +96,27 @@ struct GlobalCodes {
         for (int k = 0; k < kU; ++k)
             if (k < n) cp[(int64_t)(j0 + k) << 5] = (uint8_t)c[k];
     }
-    __device__ __forceinline__ void put(Batch &, int j0, int k, int c) const {
-        cp[(int64_t)(j0 + k) << 5] = (uint8_t)c;
+    __device__ __forceinline__ void move(Batch &, int j0, int k, int c, uint32_t sgn) const {
+        cp[(int64_t)(j0 + k) << 5] = (uint8_t)(sgn ? c - 1 : c + 1);
     }
     __device__ __forceinline__ void flush(Batch &, int) const {}
 };
 // SmemCodes<BITS>: packed in shared memory, BITS = 4 (B <= 4: one 32-bit word
 // per batch) or 8 (B <= 8: two words per batch); word w of the lane at
 // cw[w * 32] (the 32 lanes' words of one index are consecutive: no bank
-// conflict).  A move inserts its code into the batch's word in a register;
-// a batch with a move is stored back once, after its steps.
+// conflict).  A move adds +-1 to its code's field of the batch's word in a
+// register (the range check keeps the field in [0, cmax]: no carry into the
+// next field); the batch is stored back once, after its steps.
 template <int BITS> struct SmemCodes {
     uint32_t *cw;
     static constexpr int kMinB = BITS == 4 ? 1 : 5, kMaxB = BITS;
     static constexpr int kWords = BITS / 4;  // words per batch
     struct Batch {
         uint32_t w[kWords];
-        bool dirty;
     };
     __device__ __forceinline__ void load(int j0, Batch &bt, int (&c)[kU], int) const {
 #pragma unroll
         for (int i = 0; i < kWords; ++i) bt.w[i] = cw[((j0 >> 3) * kWords + i) << 5];
-        bt.dirty = false;
 #pragma unroll
         for (int k = 0; k < kU; ++k)
             c[k] = (int)((bt.w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
@@ -131,18 +131,13 @@ template <int BITS> struct SmemCodes {
 #pragma unroll
         for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = w[i];
     }
-    __device__ __forceinline__ void put(Batch &bt, int, int k, int c) const {
-        constexpr uint32_t mask = (1u << BITS) - 1u;
-        const int sh = (k * BITS) & 31;
-        uint32_t &w = bt.w[k * BITS / 32];
-        w = (w & ~(mask << sh)) | ((uint32_t)c << sh);
-        bt.dirty = true;
+    __device__ __forceinline__ void move(Batch &bt, int, int k, int, uint32_t sgn) const {
+        const uint32_t one = 1u << ((k * BITS) & 31);
+        bt.w[k * BITS / 32] += sgn ? 0u - one : one;
     }
     __device__ __forceinline__ void flush(Batch &bt, int j0) const {
-        if (bt.dirty) {
 #pragma unroll
-            for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = bt.w[i];
-        }
+        for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = bt.w[i];
     }
 };
 
@@ -198,17 +193,25 @@ struct LaneState {
 // float 1.5 * 2^23 + (2c - cmax) exactly (unit spacing there), ubias =
 // 0x4B400000 - cmax; s = sign(T) (+ for T = +0); s*u < cmax is the range
 // check of c + s.
-__device__ __forceinline__ int caq_step(LaneState &L, float x, int c, int ubias, float cmaxf,
-                                        bool &accepted) {
+__device__ __forceinline__ bool caq_move(LaneState &L, float x, int c, int ubias, float cmaxf,
+                                         uint32_t &sgn) {
     const float u = __int_as_float(ubias + 2 * c) - 12582912.f;
     const float xS = x * L.S;
     const float T = fmaf(-u, L.I, xS);
-    const uint32_t sgn = __float_as_uint(T) & 0x80000000u;
+    sgn = __float_as_uint(T) & 0x80000000u;
     const float su = __uint_as_float(__float_as_uint(u) ^ sgn);
     if (su < cmaxf && fmaf(fabsf(T), L.I, x * xS) > L.I2) {
         L.I = fmaf(__uint_as_float(0x40000000u | sgn), x, L.I);
         L.S = fmaf(4.f, su, L.S + 4.f);
         L.I2 = L.I * L.I;
+        return true;
+    }
+    return false;
+}
+__device__ __forceinline__ int caq_step(LaneState &L, float x, int c, int ubias, float cmaxf,
+                                        bool &accepted) {
+    uint32_t sgn;
+    if (caq_move(L, x, c, ubias, cmaxf, sgn)) {
         c = sgn ? c - 1 : c + 1;
         accepted = true;
     }
@@ -235,14 +238,15 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
     for (int p = 0; p < NW; ++p) w[p] = 0ull;
     int Si = 0;
     typename CS::Batch bb, bn;  // the current and the next batch's code state
+    // returns the code after the step when the round packs (else unused)
     auto step = [&](float x, int c, int j0, int k) {
-        bool accepted = false;
-        c = caq_step(L, x, c, ubias, cmaxf, accepted);
-        if (accepted) {
-            cs.put(bb, j0, k, c);
+        uint32_t sgn;
+        const bool acc = caq_move(L, x, c, ubias, cmaxf, sgn);
+        if (acc) {
+            cs.move(bb, j0, k, c, sgn);
             moved = true;
         }
-        return c;
+        return PACK_B > 0 && acc ? (sgn ? c - 1 : c + 1) : c;
     };
     // the final codes cf[0 .. count) of the batch at j0 into the planes
     auto pack = [&](const int (&cf)[kU], int j0, int count) {
