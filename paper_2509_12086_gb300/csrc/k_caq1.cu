@@ -71,7 +71,8 @@ template <int G> struct CaqBatch {
 // Where a lane keeps its vector-segment's codes during the adjustment.  Every
 // access is by batches of kU = 8 coordinates starting at a multiple of 8,
 // through a batch state held in registers:
-//   load(j0, bt, c, n)   the codes j0 .. j0 + n - 1 into c (0 past n)
+//   load(j0, bt, n)      the batch of codes j0 .. j0 + n - 1 into bt
+//   code(bt, k)          code j0 + k of the batch (0 past n)
 //   move(bt, j0, k, c, sgn)  code j0 + k (now c) moves by one, up (sgn = 0)
 //                        or down (sgn = 0x80000000), by an accepted move
 //   flush(bt, j0)        after the batch's steps
@@ -81,16 +82,19 @@ template <int G> struct CaqBatch {
 struct GlobalCodes {
     uint8_t *cp;
     static constexpr int kMinB = 1, kMaxB = 8;
-    struct Batch {};
-    __device__ __forceinline__ void load(int j0, Batch &, int (&c)[kU], int n) const {
+    struct Batch {
+        int c[kU];
+    };
+    __device__ __forceinline__ void load(int j0, Batch &bt, int n) const {
         if (n >= kU) {
 #pragma unroll
-            for (int k = 0; k < kU; ++k) c[k] = (int)cp[(int64_t)(j0 + k) << 5];
+            for (int k = 0; k < kU; ++k) bt.c[k] = (int)cp[(int64_t)(j0 + k) << 5];
         } else {
 #pragma unroll
-            for (int k = 0; k < kU; ++k) c[k] = k < n ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
+            for (int k = 0; k < kU; ++k) bt.c[k] = k < n ? (int)cp[(int64_t)(j0 + k) << 5] : 0;
         }
     }
+    __device__ __forceinline__ int code(const Batch &bt, int k) const { return bt.c[k]; }
     __device__ __forceinline__ void write(int j0, const int (&c)[kU], int n) const {
 #pragma unroll
         for (int k = 0; k < kU; ++k)
@@ -114,12 +118,12 @@ template <int BITS> struct SmemCodes {
     struct Batch {
         uint32_t w[kWords];
     };
-    __device__ __forceinline__ void load(int j0, Batch &bt, int (&c)[kU], int) const {
+    __device__ __forceinline__ void load(int j0, Batch &bt, int) const {
 #pragma unroll
         for (int i = 0; i < kWords; ++i) bt.w[i] = cw[((j0 >> 3) * kWords + i) << 5];
-#pragma unroll
-        for (int k = 0; k < kU; ++k)
-            c[k] = (int)((bt.w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
+    }
+    __device__ __forceinline__ int code(const Batch &bt, int k) const {
+        return (int)((bt.w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
     }
     __device__ __forceinline__ void write(int j0, const int (&c)[kU], int n) const {
         uint32_t w[kWords];
@@ -152,9 +156,11 @@ __device__ __forceinline__ int pack_segment(const CS &cs, int len, bool valid,
     for (int p = 0; p < B; ++p) w[p] = 0ull;
     int S = 0;
     for (int j0 = 0; j0 < len; j0 += kU) {
-        int c[kU];
         typename CS::Batch bt;
-        cs.load(j0, bt, c, len - j0);
+        cs.load(j0, bt, len - j0);
+        int c[kU];
+#pragma unroll
+        for (int k = 0; k < kU; ++k) c[k] = cs.code(bt, k);
         // plane p of the kU codes as the bits of one byte (past the end: 0)
 #pragma unroll
         for (int p = 0; p < B; ++p) {
@@ -238,8 +244,11 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
     for (int p = 0; p < NW; ++p) w[p] = 0ull;
     int Si = 0;
     typename CS::Batch bb, bn;  // the current and the next batch's code state
+    // the step of coordinate j0 + k (its code read from the batch state just
+    // before the step: earlier moves of the batch touch only other codes);
     // returns the code after the step when the round packs (else unused)
-    auto step = [&](float x, int c, int j0, int k) {
+    auto step = [&](float x, int j0, int k) {
+        const int c = cs.code(bb, k);
         uint32_t sgn;
         const bool acc = caq_move(L, x, c, ubias, cmaxf, sgn);
         if (acc) {
@@ -274,13 +283,11 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
         }
     };
     float xb[kU];
-    int cb[kU];
 #pragma unroll
     for (int k = 0; k < kU; ++k) xb[k] = k < len ? __ldg(op + ((int64_t)k << 5)) : 0.f;
-    cs.load(0, bb, cb, len);
+    cs.load(0, bb, len);
     for (int j0 = 0; j0 < lenU; j0 += kU) {
         float xn[kU];
-        int cn[kU];
         if (j0 + 2 * kU <= len) {  // the next batch lies inside the segment
 #pragma unroll
             for (int k = 0; k < kU; ++k) xn[k] = __ldg(op + ((int64_t)(j0 + kU + k) << 5));
@@ -293,24 +300,21 @@ __device__ __forceinline__ int run_round(LaneState &L, const float *op, const CS
         }
         // the next batch's codes (a code is written at its own step, and a
         // batch is stored back after its steps: the next one is current)
-        if (j0 + kU < len) cs.load(j0 + kU, bn, cn, len - j0 - kU);
+        if (j0 + kU < len) cs.load(j0 + kU, bn, len - j0 - kU);
         int cf[kU];
 #pragma unroll
-        for (int k = 0; k < kU; ++k) cf[k] = step(xb[k], cb[k], j0, k);
+        for (int k = 0; k < kU; ++k) cf[k] = step(xb[k], j0, k);
         cs.flush(bb, j0);
         pack(cf, j0, kU);
         bb = bn;
 #pragma unroll
-        for (int k = 0; k < kU; ++k) {
-            xb[k] = xn[k];
-            cb[k] = cn[k];
-        }
+        for (int k = 0; k < kU; ++k) xb[k] = xn[k];
     }
     // the last, partial batch
     if (lenU < len) {
         int cf[kU];
 #pragma unroll
-        for (int k = 0; k < kU; ++k) cf[k] = lenU + k < len ? step(xb[k], cb[k], lenU, k) : 0;
+        for (int k = 0; k < kU; ++k) cf[k] = lenU + k < len ? step(xb[k], lenU, k) : 0;
         cs.flush(bb, lenU);
         pack(cf, lenU, len - lenU);
     }
