@@ -26,6 +26,7 @@
 // bit-planes, during the last round (or, for a warp whose lanes all stop
 // earlier, in a pass of its own).
 #include <algorithm>
+#include <atomic>
 
 #include "saq_internal.h"
 
@@ -500,15 +501,28 @@ k_caq1_sm(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTa
 // The rows of up to kMaxGroups models (a batch of several collections) in
 // one launch: global warp w belongs to the group g with warp_start[g] <= w <
 // warp_start[g + 1].
-__global__ void __launch_bounds__(256, 4)
-k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch) {
+template <bool SMEM_CODES>
+__device__ __forceinline__ void caq1_grouped_warp(const CaqBatch<kMaxGroups> &batch,
+                                                  uint32_t *smem_codes, int words_per_lane) {
     const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int gi = 0;
     while (gi + 1 < batch.ngroups && wg >= batch.warp_start[gi + 1]) ++gi;
     if (wg >= batch.warp_start[batch.ngroups]) return;  // uniform per warp
     const CaqGroup &P = batch.g[gi];
-    caq1_warp<false>(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds, P.cs,
-                     P.vmax, P.codes, P.code_stride, P.factors, P.nf, nullptr, 0);
+    caq1_warp<SMEM_CODES>(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds, P.cs,
+                          P.vmax, P.codes, P.code_stride, P.factors, P.nf, smem_codes,
+                          words_per_lane);
+}
+__global__ void __launch_bounds__(256, 4)
+k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch) {
+    caq1_grouped_warp<false>(batch, nullptr, 0);
+}
+// The same with the codes in shared memory (words_per_lane: the largest
+// over the groups' segments).
+__global__ void __launch_bounds__(256, 4)
+k_caq1_grouped_sm(const __grid_constant__ CaqBatch<kMaxGroups> batch, int words_per_lane) {
+    extern __shared__ uint32_t smem_codes[];
+    caq1_grouped_warp<true>(batch, smem_codes, words_per_lane);
 }
 
 // The instruction ceiling of the adjustment: caq_step on coordinates held in
@@ -608,6 +622,37 @@ saq_status make_group(const CaqJob &j, CaqGroup *g) {
     return SAQ_OK;
 }
 
+// 32-bit words per lane of the shared-memory code store for model m: one per
+// 8 coordinates of its longest segment (4-bit codes) or two (bytes).
+int words_per_lane(const saq_model *m) {
+    int wpl = 0;
+    for (const KeptSeg &k : m->kept) wpl = std::max(wpl, (k.len + 7) / 8 * (k.bits <= 4 ? 1 : 2));
+    return wpl;
+}
+
+// Shared memory of a block of 8 warps for wpl words per lane; the codes go
+// to shared memory when it is at most kCaqSmemMax (at least 3 blocks per SM).
+size_t caq_smem_bytes(int wpl) { return (size_t)wpl * 32 * 4 * 8; }
+
+// Sets the kernel's shared-memory attributes once per device (`done`: one
+// bit per device ordinal, devices 0..63; a larger ordinal sets them at
+// every launch).
+template <class K> saq_status prepare_smem_kernel(K *kernel, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    SAQ_CUDA_CHECK(cudaGetDevice(&dev));
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return SAQ_OK;
+    SAQ_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kCaqSmemMax));
+    // all of the unified L1 / shared storage as shared memory: four blocks
+    // of 56 KB fit (the d = 960 plan's longest segment)
+    SAQ_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        100));
+    done.fetch_or(bit, std::memory_order_release);
+    return SAQ_OK;
+}
+std::atomic<uint64_t> g_caq1_sm_ready{0}, g_caq1_grouped_sm_ready{0};
+
 }  // namespace
 
 saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *cs,
@@ -618,22 +663,16 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
     if (st != SAQ_OK) return st;
     const int64_t warps = (n + 31) / 32 * g.nseg;
     const int64_t blocks = (warps + 7) / 8;
-    // codes in shared memory when a block of 8 warps needs at most 72 KB
-    // (at least 3 blocks per SM); otherwise in the global byte scratch
-    int wpl = 0;  // 32-bit words per lane: one per 8 coordinates (4-bit codes) or two (bytes)
-    for (const KeptSeg &k : m->kept) wpl = std::max(wpl, (k.len + 7) / 8 * (k.bits <= 4 ? 1 : 2));
-    const size_t smem = (size_t)wpl * 32 * 4 * 8;
+    // codes in shared memory when they fit, else in the global byte scratch
+    const int wpl = words_per_lane(m);
+    const size_t smem = caq_smem_bytes(wpl);
+    if (smem <= kCaqSmemMax) {
+        st = prepare_smem_kernel(k_caq1_sm, g_caq1_sm_ready);
+        if (st != SAQ_OK) return st;
+    }
     {
         LaunchTimer lt_(kKindQuantize, s);
         if (smem <= kCaqSmemMax) {
-            SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_caq1_sm,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)kCaqSmemMax));
-            // all of the unified L1 / shared storage as shared memory: four
-            // blocks of 56 KB fit (the d = 960 plan's longest segment)
-            SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_caq1_sm,
-                                                cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                100));
             k_caq1_sm<<<(unsigned)blocks, 256, smem, s>>>(Oi, n, g.dk, g.nseg, g.t, g.rounds, vmax,
                                                           codes, g.code_stride, factors, g.nf, wpl);
         } else {
@@ -652,8 +691,10 @@ saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s) {
     CaqBatch<kMaxGroups> b;
     b.ngroups = 0;
     b.warp_start[0] = 0;
+    int wpl = 0;
     for (int i = 0; i < njobs; ++i) {
         if (jobs[i].n <= 0 || jobs[i].m->kept.empty()) continue;
+        wpl = std::max(wpl, words_per_lane(jobs[i].m));
         saq_status st = make_group(jobs[i], &b.g[b.ngroups]);
         if (st != SAQ_OK) return st;
         b.warp_start[b.ngroups + 1] =
@@ -662,9 +703,17 @@ saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s) {
     }
     if (b.ngroups == 0) return SAQ_OK;
     const int64_t blocks = (b.warp_start[b.ngroups] + 7) / 8;
+    const size_t smem = caq_smem_bytes(wpl);
+    if (smem <= kCaqSmemMax) {
+        saq_status st = prepare_smem_kernel(k_caq1_grouped_sm, g_caq1_grouped_sm_ready);
+        if (st != SAQ_OK) return st;
+    }
     {
         LaunchTimer lt_(kKindQuantize, s);
-        k_caq1_grouped<<<(unsigned)blocks, 256, 0, s>>>(b);
+        if (smem <= kCaqSmemMax)
+            k_caq1_grouped_sm<<<(unsigned)blocks, 256, smem, s>>>(b, wpl);
+        else
+            k_caq1_grouped<<<(unsigned)blocks, 256, 0, s>>>(b);
     }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
