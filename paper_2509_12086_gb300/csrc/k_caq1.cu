@@ -106,22 +106,54 @@ struct GlobalCodes {
     }
     __device__ __forceinline__ void flush(Batch &, int) const {}
 };
-// SmemCodes<BITS>: packed in shared memory, BITS = 4 (B <= 4: one 32-bit word
-// per batch) or 8 (B <= 8: two words per batch); word w of the lane at
-// cw[w * 32] (the 32 lanes' words of one index are consecutive: no bank
-// conflict).  A move adds +-1 to its code's field of the batch's word in a
-// register (the range check keeps the field in [0, cmax]: no carry into the
-// next field); the batch is stored back once, after its steps.
+// SmemCodes<BITS>: packed in shared memory, BITS bits per code: 1 (B = 1),
+// 2 (B = 2), 4 (B = 3, 4) or 8 (B = 5 .. 8).  A batch of 8 codes takes BITS
+// bytes of the lane's byte stream, whose byte b is byte b % 4 of the lane's
+// word b / 4, and word w of the lane sits at cw[w * 32] (the 32 lanes' words
+// of one index are consecutive: no bank conflict).  A move adds +-1 to its
+// code's field of the batch's value in a register (the range check keeps
+// the field in [0, cmax]: no carry into the next field); the batch is stored
+// back once, after its steps, as a byte, a half-word or one or two words, so
+// that no other batch's codes are rewritten.
 template <int BITS> struct SmemCodes {
     uint32_t *cw;
-    static constexpr int kMinB = BITS == 4 ? 1 : 5, kMaxB = BITS;
-    static constexpr int kWords = BITS / 4;  // words per batch
+    static constexpr int kMinB = BITS == 1 ? 1 : BITS == 2 ? 2 : BITS == 4 ? 3 : 5, kMaxB = BITS;
+    static constexpr int kWords = BITS >= 4 ? BITS / 4 : 1;  // registers per batch
     struct Batch {
         uint32_t w[kWords];
     };
-    __device__ __forceinline__ void load(int j0, Batch &bt, int) const {
+    // the batch of coordinates j0 .. j0 + 7: its first word (BITS >= 4) or
+    // its byte (BITS < 4)
+    __device__ __forceinline__ uint32_t *word_of(int j0) const {
+        return cw + (((j0 >> 3) * kWords) << 5);
+    }
+    __device__ __forceinline__ uint8_t *byte_of(int j0) const {
+        const int bo = (j0 >> 3) * BITS;
+        return reinterpret_cast<uint8_t *>(cw + ((bo >> 2) << 5)) + (bo & 3);
+    }
+    __device__ __forceinline__ uint32_t get(int j0) const {
+        if constexpr (BITS == 1) return *byte_of(j0);
+        else return *reinterpret_cast<const uint16_t *>(byte_of(j0));
+    }
+    __device__ __forceinline__ void set(int j0, uint32_t v) const {
+        if constexpr (BITS == 1) *byte_of(j0) = (uint8_t)v;
+        else *reinterpret_cast<uint16_t *>(byte_of(j0)) = (uint16_t)v;
+    }
+    __device__ __forceinline__ void store(int j0, const uint32_t (&w)[kWords]) const {
+        if constexpr (BITS >= 4) {
 #pragma unroll
-        for (int i = 0; i < kWords; ++i) bt.w[i] = cw[((j0 >> 3) * kWords + i) << 5];
+            for (int i = 0; i < kWords; ++i) word_of(j0)[i << 5] = w[i];
+        } else {
+            set(j0, w[0]);
+        }
+    }
+    __device__ __forceinline__ void load(int j0, Batch &bt, int) const {
+        if constexpr (BITS >= 4) {
+#pragma unroll
+            for (int i = 0; i < kWords; ++i) bt.w[i] = word_of(j0)[i << 5];
+        } else {
+            bt.w[0] = get(j0);
+        }
     }
     __device__ __forceinline__ int code(const Batch &bt, int k) const {
         return (int)((bt.w[k * BITS / 32] >> ((k * BITS) & 31)) & ((1u << BITS) - 1u));
@@ -133,17 +165,13 @@ template <int BITS> struct SmemCodes {
 #pragma unroll
         for (int k = 0; k < kU; ++k)
             if (k < n) w[k * BITS / 32] |= (uint32_t)c[k] << ((k * BITS) & 31);
-#pragma unroll
-        for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = w[i];
+        store(j0, w);
     }
     __device__ __forceinline__ void move(Batch &bt, int, int k, int, uint32_t sgn) const {
         const uint32_t one = 1u << ((k * BITS) & 31);
         bt.w[k * BITS / 32] += sgn ? 0u - one : one;
     }
-    __device__ __forceinline__ void flush(Batch &bt, int j0) const {
-#pragma unroll
-        for (int i = 0; i < kWords; ++i) cw[((j0 >> 3) * kWords + i) << 5] = bt.w[i];
-    }
+    __device__ __forceinline__ void flush(Batch &bt, int j0) const { store(j0, bt.w); }
 };
 
 // Bit-planes of one lane's segment from its codes (most significant first,
@@ -461,7 +489,11 @@ __device__ __forceinline__ void caq1_warp(int64_t w, const float *__restrict__ O
     float *fo = factors + v * nf + fidx;
     if constexpr (SMEM_CODES) {
         uint32_t *cw = smem_codes + (threadIdx.x >> 5) * (words_per_lane << 5) + lane;
-        if (B <= 4)  // uniform per warp
+        if (B == 1)  // uniform per warp
+            caq_segment(SmemCodes<1>{cw}, op, len, B, words, valid, vmax, rounds, cout, fo);
+        else if (B == 2)
+            caq_segment(SmemCodes<2>{cw}, op, len, B, words, valid, vmax, rounds, cout, fo);
+        else if (B <= 4)
             caq_segment(SmemCodes<4>{cw}, op, len, B, words, valid, vmax, rounds, cout, fo);
         else
             caq_segment(SmemCodes<8>{cw}, op, len, B, words, valid, vmax, rounds, cout, fo);
@@ -622,11 +654,15 @@ saq_status make_group(const CaqJob &j, CaqGroup *g) {
     return SAQ_OK;
 }
 
-// 32-bit words per lane of the shared-memory code store for model m: one per
-// 8 coordinates of its longest segment (4-bit codes) or two (bytes).
+// 32-bit words per lane of the shared-memory code store for model m: its
+// largest segment's, at 1, 2, 4 or 8 bits per code (B = 1, 2, 3-4, 5-8),
+// a batch of 8 codes in that many bytes.
 int words_per_lane(const saq_model *m) {
     int wpl = 0;
-    for (const KeptSeg &k : m->kept) wpl = std::max(wpl, (k.len + 7) / 8 * (k.bits <= 4 ? 1 : 2));
+    for (const KeptSeg &k : m->kept) {
+        const int width = k.bits <= 1 ? 1 : k.bits == 2 ? 2 : k.bits <= 4 ? 4 : 8;
+        wpl = std::max(wpl, ((k.len + 7) / 8 * width + 3) / 4);
+    }
     return wpl;
 }
 
