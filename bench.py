@@ -43,9 +43,9 @@ NCU_TRAFFIC = {
     "projection": {"src": "k_tc.cu", "sha1": "ee2a1a97648132496c5cf86ca543173524ad3b1c",
                    "workload": "c2_d960", "precision": "fp32",
                    "bytes_per_row": (258274816 + 215818496) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "6f7c9ddcf0d55f2d4437a54be6534436a0fb9ddc",
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "37cb46708aaed0a6dbb6dc70dce1a5cdcda8acb6",
                              "workload": "c2_d960", "precision": "fp32",
-                             "bytes_per_row": (1982832896 + 287276032) / 65536},
+                             "bytes_per_row": (1558182400 + 35342336) / 65536},
 }
 
 
