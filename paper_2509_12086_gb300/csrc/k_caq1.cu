@@ -533,28 +533,36 @@ k_caq1_sm(const float *__restrict__ Oi, int64_t n, int dk, int nseg, const SegTa
 // The rows of up to kMaxGroups models (a batch of several collections) in
 // one launch: global warp w belongs to the group g with warp_start[g] <= w <
 // warp_start[g + 1].
+// A persistent warp of a grouped launch: it takes work items (global warp
+// indices of the batch) from the device counter `queue` until none is left.
 template <bool SMEM_CODES>
-__device__ __forceinline__ void caq1_grouped_warp(const CaqBatch<kMaxGroups> &batch,
+__device__ __forceinline__ void caq1_grouped_warp(const CaqBatch<kMaxGroups> &batch, int *queue,
                                                   uint32_t *smem_codes, int words_per_lane) {
-    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int gi = 0;
-    while (gi + 1 < batch.ngroups && wg >= batch.warp_start[gi + 1]) ++gi;
-    if (wg >= batch.warp_start[batch.ngroups]) return;  // uniform per warp
-    const CaqGroup &P = batch.g[gi];
-    caq1_warp<SMEM_CODES>(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds, P.cs,
-                          P.vmax, P.codes, P.code_stride, P.factors, P.nf, smem_codes,
-                          words_per_lane);
+    const int64_t total = batch.warp_start[batch.ngroups];
+    for (;;) {
+        int wi = 0;
+        if ((threadIdx.x & 31) == 0) wi = atomicAdd(queue, 1);
+        const int64_t wg = __shfl_sync(0xffffffffu, wi, 0);
+        if (wg >= total) break;  // uniform per warp
+        int gi = 0;
+        while (gi + 1 < batch.ngroups && wg >= batch.warp_start[gi + 1]) ++gi;
+        const CaqGroup &P = batch.g[gi];
+        caq1_warp<SMEM_CODES>(wg - batch.warp_start[gi], P.Oi, P.n, P.dk, P.nseg, P.t, P.rounds,
+                              P.cs, P.vmax, P.codes, P.code_stride, P.factors, P.nf, smem_codes,
+                              words_per_lane);
+    }
 }
 __global__ void __launch_bounds__(256, 4)
-k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch) {
-    caq1_grouped_warp<false>(batch, nullptr, 0);
+k_caq1_grouped(const __grid_constant__ CaqBatch<kMaxGroups> batch, int *queue) {
+    caq1_grouped_warp<false>(batch, queue, nullptr, 0);
 }
 // The same with the codes in shared memory (words_per_lane: the largest
 // over the groups' segments).
 __global__ void __launch_bounds__(256, 4)
-k_caq1_grouped_sm(const __grid_constant__ CaqBatch<kMaxGroups> batch, int words_per_lane) {
+k_caq1_grouped_sm(const __grid_constant__ CaqBatch<kMaxGroups> batch, int *queue,
+                  int words_per_lane) {
     extern __shared__ uint32_t smem_codes[];
-    caq1_grouped_warp<true>(batch, smem_codes, words_per_lane);
+    caq1_grouped_warp<true>(batch, queue, smem_codes, words_per_lane);
 }
 
 // The instruction ceiling of the adjustment: caq_step on coordinates held in
@@ -721,7 +729,7 @@ saq_status launch_caq1(const saq_model *m, const float *Oi, int64_t n, uint8_t *
     return SAQ_OK;
 }
 
-saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s) {
+saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, int *queue, cudaStream_t s) {
     if (njobs < 1 || njobs > kMaxGroups)
         return set_error(SAQ_ERR_INVALID, "1..%d models per grouped launch", kMaxGroups);
     CaqBatch<kMaxGroups> b;
@@ -738,18 +746,31 @@ saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s) {
         ++b.ngroups;
     }
     if (b.ngroups == 0) return SAQ_OK;
+    if (b.warp_start[b.ngroups] > 0x7FFFFFFF)
+        return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
     const int64_t blocks = (b.warp_start[b.ngroups] + 7) / 8;
     const size_t smem = caq_smem_bytes(wpl);
-    if (smem <= kCaqSmemMax) {
+    const bool sm_codes = smem <= kCaqSmemMax;
+    if (sm_codes) {
         saq_status st = prepare_smem_kernel(k_caq1_grouped_sm, g_caq1_grouped_sm_ready);
         if (st != SAQ_OK) return st;
     }
+    // persistent: as many blocks as stay resident at once (at most the work)
+    int dev = 0, sms = 0, per_sm = 0;
+    SAQ_CUDA_CHECK(cudaGetDevice(&dev));
+    SAQ_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (sm_codes)
+        SAQ_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_caq1_grouped_sm, 256,
+                                                                     smem));
+    else
+        SAQ_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_caq1_grouped, 256, 0));
+    const int64_t grid = std::min<int64_t>(blocks, (int64_t)std::max(1, sms * per_sm));
     {
         LaunchTimer lt_(kKindQuantize, s);
-        if (smem <= kCaqSmemMax)
-            k_caq1_grouped_sm<<<(unsigned)blocks, 256, smem, s>>>(b, wpl);
+        if (sm_codes)
+            k_caq1_grouped_sm<<<(unsigned)grid, 256, smem, s>>>(b, queue, wpl);
         else
-            k_caq1_grouped<<<(unsigned)blocks, 256, 0, s>>>(b);
+            k_caq1_grouped<<<(unsigned)grid, 256, 0, s>>>(b, queue);
     }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());

@@ -120,10 +120,13 @@ static_assert(Cfg<kSplit>::STAGES * stage_bytes<kSplit>() > 228u * 1024u / 2u &&
                   Cfg<kBF16>::STAGES * stage_bytes<kBF16>() > 228u * 1024u / 2u &&
                   Cfg<kFP8>::STAGES * stage_bytes<kFP8>() > 228u * 1024u / 2u,
               "two CTAs per SM would share 512 TMEM columns");
-// barriers (full, conv, empty per stage; the accumulator's), the TMEM address
-// and the abort flag, ahead of the row-norm halves
+// barriers (full, conv, empty per stage; the accumulator's; for the
+// persistent kernel the tile ring's two full and two empty and acc_empty, and
+// the ring), the TMEM address and the abort flag, ahead of the row-norm halves
 constexpr uint32_t kBarArea = 256;
-template <int MODE> constexpr uint32_t bar_bytes() { return 3u * 8u * Cfg<MODE>::STAGES + 8u + 8u; }
+template <int MODE> constexpr uint32_t bar_bytes() {
+    return 3u * 8u * Cfg<MODE>::STAGES + 8u + 4u * 8u + 8u + 2u * 8u + 8u;
+}
 static_assert(bar_bytes<kSplit>() <= kBarArea && bar_bytes<kBF16>() <= kBarArea &&
                   bar_bytes<kFP8>() <= kBarArea,
               "barriers overflow their shared-memory area");
@@ -322,6 +325,161 @@ __device__ __forceinline__ uint32_t swz128(int r, int c) {
     return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
+// One K block of one tile row: the row's staged X values (stage st, row r)
+// centred and scaled with one FMA against -c * s (mk), converted into the A
+// operand words (split: hi in wa, lo in wl), and their squares added to nrm.
+template <int MODE>
+__device__ __forceinline__ void convert_block(const uint8_t *st, const float *mk, int r,
+                                              float x_scale, float &nrm, uint32_t (&wa)[16],
+                                              uint32_t (&wl)[16]) {
+    if (MODE == kFP8) {
+        // 4 chunks of 16 E4M3 (64 values) per thread, from the two staged boxes
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int ac = i;  // operand chunk: values ac*16 .. ac*16+15
+            const uint8_t *xb = st + (i >> 1) * kXBox;
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = (i & 1) * 4 + e;  // staged chunk within its box
+                const float4 x = *reinterpret_cast<const float4 *>(xb + swz128(r, c));
+                const float4 m = *reinterpret_cast<const float4 *>(mk + ac * 16 + e * 4);
+                const float y0 = fmaf(x.x, x_scale, m.x), y1 = fmaf(x.y, x_scale, m.y);
+                const float y2 = fmaf(x.z, x_scale, m.z), y3 = fmaf(x.w, x_scale, m.w);
+                nrm = fmaf(y0, y0, nrm); nrm = fmaf(y1, y1, nrm);
+                nrm = fmaf(y2, y2, nrm); nrm = fmaf(y3, y3, nrm);
+                const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+                    make_float2(y0, y1), __NV_SATFINITE, __NV_E4M3);
+                const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                    make_float2(y2, y3), __NV_SATFINITE, __NV_E4M3);
+                w[e] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 16i + 4e .. + 3
+        }
+    } else {
+        // 4 chunks of 8 values (32 values) per thread from the staged box
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int ac = i;  // operand chunk: values ac*8 .. ac*8+7
+            const float4 x0 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac));
+            const float4 x1 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac + 1));
+            const float4 m0 = *reinterpret_cast<const float4 *>(mk + ac * 8);
+            const float4 m1 = *reinterpret_cast<const float4 *>(mk + ac * 8 + 4);
+            float y[8] = {fmaf(x0.x, x_scale, m0.x), fmaf(x0.y, x_scale, m0.y),
+                          fmaf(x0.z, x_scale, m0.z), fmaf(x0.w, x_scale, m0.w),
+                          fmaf(x1.x, x_scale, m1.x), fmaf(x1.y, x_scale, m1.y),
+                          fmaf(x1.z, x_scale, m1.z), fmaf(x1.w, x_scale, m1.w)};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) nrm = fmaf(y[e], y[e], nrm);
+            if (MODE == kBF16) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    w[e] = pack_b2(__floats2bfloat162_rn(y[2 * e], y[2 * e + 1]));
+#pragma unroll
+                for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 8i + 2e, + 1
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {  // values 8i + 2e, + 1
+                    const __half2 hh = __floats2half2_rn(y[2 * e], y[2 * e + 1]);
+                    const float2 hf = __half22float2(hh);
+                    wa[4 * i + e] = pack_h2(hh);
+                    wl[4 * i + e] =
+                        pack_h2(__floats2half2_rn(y[2 * e] - hf.x, y[2 * e + 1] - hf.y));
+                }
+            }
+        }
+    }
+}
+
+// The epilogue of one tile row (thread of row r in lane quadrant tq, column
+// blocks h, h + 2, ... of 32): accumulator columns scaled per output column
+// into O (row-major with stride ldo, or interleaved by groups of 32 rows when
+// il), and with vmax != NULL the running max |o| of each kept segment.
+template <int MODE>
+__device__ __forceinline__ void tile_epilogue(uint32_t tq, int h, int lane, int r, int64_t row0,
+                                              bool row_ok, int np, int col0, int dk,
+                                              const float *__restrict__ col_scale,
+                                              float *__restrict__ O, int64_t ldo, int il,
+                                              float *__restrict__ vmax, const SegCols &segc) {
+    float *orow = O + (row0 + r) * ldo;
+    // interleaved: column `col` of row R at ((R / 32) * dk + col) * 32 + R % 32
+    float *ogrp = O + (((row0 + r) >> 5) * (int64_t)dk << 5) + lane;
+    // running max |o| of the current kept segment (interleaved layout only)
+    const bool want_vmax = il && vmax != nullptr;
+    float *vgrp = want_vmax ? vmax + (((row0 + r) >> 5) * (int64_t)segc.nk << 5) + lane
+                            : nullptr;
+    int si = 0;
+    float mx = 0.f;
+    // 32-column blocks, alternating between the two threads of a row; a
+    // block past np reads accumulator columns the allocation holds
+    // (np <= 256) and scales from the padded scale vector
+#pragma unroll 1
+    for (int b = h; b < ((np + 31) >> 5); b += 2) {
+        const int c = b << 5;
+        const int cb = col0 + c;  // first output column of the block
+        float4 sc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sc[i] = __ldg(reinterpret_cast<const float4 *>(col_scale + cb) + i);
+        float v[32];
+        if (MODE == kSplit) {
+            float v2[32];
+            tmem_ld32x2(tq + (uint32_t)c, tq + (uint32_t)(kAcc2 + c), v, v2);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += v2[i];
+        } else {
+            tmem_ld32(tq + (uint32_t)c, v);
+        }
+        if (!row_ok || cb >= dk) continue;
+        const int cn = min(min(32, np - c), dk - cb);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            v[4 * i] *= sc[i].x; v[4 * i + 1] *= sc[i].y;
+            v[4 * i + 2] *= sc[i].z; v[4 * i + 3] *= sc[i].w;
+        }
+        if (cn == 32) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
+                else orow[cb + i] = v[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (i >= cn) break;
+                if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
+                else orow[cb + i] = v[i];
+            }
+        }
+        if (want_vmax) {
+            while (cb >= segc.end[si]) {
+                if (mx > 0.f) atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+                mx = 0.f;
+                ++si;
+            }
+            if (cb + cn <= segc.end[si]) {  // the block lies in one segment
+#pragma unroll
+                for (int i = 0; i < 32; ++i) mx = fmaxf(mx, i < cn ? fabsf(v[i]) : 0.f);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i >= cn) break;
+                    while (cb + i >= segc.end[si]) {
+                        if (mx > 0.f)
+                            atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+                        mx = 0.f;
+                        ++si;
+                    }
+                    mx = fmaxf(mx, fabsf(v[i]));
+                }
+            }
+        }
+    }
+    if (want_vmax && row_ok && mx > 0.f)
+        atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+}
+
 // The work of one CTA: row tile `tile`, column pass `pass` of one model
 // (tmx: the tensor map of its X rows, in parameter space).
 template <int MODE>
@@ -468,65 +626,7 @@ __device__ __forceinline__ void proj_tile(
             const float *mk = mcs + kb * C::BK;
             uint32_t wa[16];  // the row's A values of the stage (split: the hi part)
             uint32_t wl[16];  // split: the lo part
-            if (MODE == kFP8) {
-                // 4 chunks of 16 E4M3 (64 values) per thread, from the two staged boxes
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int ac = i;  // operand chunk: values ac*16 .. ac*16+15
-                    const uint8_t *xb = st + (i >> 1) * kXBox;
-                    uint32_t w[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = (i & 1) * 4 + e;  // staged chunk within its box
-                        const float4 x = *reinterpret_cast<const float4 *>(xb + swz128(r, c));
-                        const float4 m = *reinterpret_cast<const float4 *>(mk + ac * 16 + e * 4);
-                        const float y0 = fmaf(x.x, x_scale, m.x), y1 = fmaf(x.y, x_scale, m.y);
-                        const float y2 = fmaf(x.z, x_scale, m.z), y3 = fmaf(x.w, x_scale, m.w);
-                        nrm = fmaf(y0, y0, nrm); nrm = fmaf(y1, y1, nrm);
-                        nrm = fmaf(y2, y2, nrm); nrm = fmaf(y3, y3, nrm);
-                        const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
-                            make_float2(y0, y1), __NV_SATFINITE, __NV_E4M3);
-                        const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-                            make_float2(y2, y3), __NV_SATFINITE, __NV_E4M3);
-                        w[e] = (uint32_t)lo | ((uint32_t)hi << 16);
-                    }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 16i + 4e .. + 3
-                }
-            } else {
-                // 4 chunks of 8 values (32 values) per thread from the staged box
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int ac = i;  // operand chunk: values ac*8 .. ac*8+7
-                    const float4 x0 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac));
-                    const float4 x1 = *reinterpret_cast<const float4 *>(st + swz128(r, 2 * ac + 1));
-                    const float4 m0 = *reinterpret_cast<const float4 *>(mk + ac * 8);
-                    const float4 m1 = *reinterpret_cast<const float4 *>(mk + ac * 8 + 4);
-                    float y[8] = {fmaf(x0.x, x_scale, m0.x), fmaf(x0.y, x_scale, m0.y),
-                                  fmaf(x0.z, x_scale, m0.z), fmaf(x0.w, x_scale, m0.w),
-                                  fmaf(x1.x, x_scale, m1.x), fmaf(x1.y, x_scale, m1.y),
-                                  fmaf(x1.z, x_scale, m1.z), fmaf(x1.w, x_scale, m1.w)};
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) nrm = fmaf(y[e], y[e], nrm);
-                    if (MODE == kBF16) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            w[e] = pack_b2(__floats2bfloat162_rn(y[2 * e], y[2 * e + 1]));
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) wa[4 * i + e] = w[e];  // values 8i + 2e, + 1
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {  // values 8i + 2e, + 1
-                            const __half2 hh = __floats2half2_rn(y[2 * e], y[2 * e + 1]);
-                            const float2 hf = __half22float2(hh);
-                            wa[4 * i + e] = pack_h2(hh);
-                            wl[4 * i + e] =
-                                pack_h2(__floats2half2_rn(y[2 * e] - hf.x, y[2 * e + 1] - hf.y));
-                        }
-                    }
-                }
-            }
+            convert_block<MODE>(st, mk, r, x_scale, nrm, wa, wl);
             // TMEM column c of a buffer holds the row's values of K offsets
             // c * (4 / element bytes) upward, lowest in the low bits
             tmem_st16(tq + ta_col<MODE>(s, 0), wa);
@@ -554,81 +654,8 @@ __device__ __forceinline__ void proj_tile(
         ready = __shfl_sync(0xffffffffu, ready, 0);
         if (ready) {
             tc_fence_after();
-            float *orow = O + (row0 + r) * ldo;
-            // interleaved: column `col` of row R at ((R / 32) * dk + col) * 32 + R % 32
-            float *ogrp = O + (((row0 + r) >> 5) * (int64_t)dk << 5) + lane;
-            // running max |o| of the current kept segment (interleaved layout only)
-            const bool want_vmax = il && vmax != nullptr;
-            float *vgrp = want_vmax ? vmax + (((row0 + r) >> 5) * (int64_t)segc.nk << 5) + lane
-                                    : nullptr;
-            int si = 0;
-            float mx = 0.f;
-            // 32-column blocks, alternating between the two threads of a row; a
-            // block past np reads accumulator columns the allocation holds
-            // (np <= 256) and scales from the padded scale vector
-#pragma unroll 1
-            for (int b = h; b < ((np + 31) >> 5); b += 2) {
-                const int c = b << 5;
-                const int cb = col0 + c;  // first output column of the block
-                float4 sc[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) sc[i] = __ldg(reinterpret_cast<const float4 *>(col_scale + cb) + i);
-                float v[32];
-                if (MODE == kSplit) {
-                    float v2[32];
-                    tmem_ld32x2(tq + (uint32_t)c, tq + (uint32_t)(kAcc2 + c), v, v2);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] += v2[i];
-                } else {
-                    tmem_ld32(tq + (uint32_t)c, v);
-                }
-                if (!row_ok || cb >= dk) continue;
-                const int cn = min(min(32, np - c), dk - cb);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    v[4 * i] *= sc[i].x; v[4 * i + 1] *= sc[i].y;
-                    v[4 * i + 2] *= sc[i].z; v[4 * i + 3] *= sc[i].w;
-                }
-                if (cn == 32) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
-                        else orow[cb + i] = v[i];
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i >= cn) break;
-                        if (il) ogrp[(int64_t)(cb + i) << 5] = v[i];
-                        else orow[cb + i] = v[i];
-                    }
-                }
-                if (want_vmax) {
-                    while (cb >= segc.end[si]) {
-                        if (mx > 0.f) atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
-                        mx = 0.f;
-                        ++si;
-                    }
-                    if (cb + cn <= segc.end[si]) {  // the block lies in one segment
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) mx = fmaxf(mx, i < cn ? fabsf(v[i]) : 0.f);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            if (i >= cn) break;
-                            while (cb + i >= segc.end[si]) {
-                                if (mx > 0.f)
-                                    atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
-                                mx = 0.f;
-                                ++si;
-                            }
-                            mx = fmaxf(mx, fabsf(v[i]));
-                        }
-                    }
-                }
-            }
-            if (want_vmax && row_ok && mx > 0.f)
-                atomicMax((int *)(vgrp + ((int64_t)si << 5)), __float_as_int(mx));
+            tile_epilogue<MODE>(tq, h, lane, r, row0, row_ok, np, col0, dk, col_scale, O, ldo, il,
+                                vmax, segc);
         }
         tc_fence_before();
     }
@@ -662,38 +689,379 @@ k_proj_tc(const __grid_constant__ CUtensorMap tmx, const uint8_t *__restrict__ w
                     err, wait_ns, norm_limit);
 }
 
-// One model's part of a grouped launch (interleaved output, v_max, norms).
+// One model's part of a launch: its rows, operands and outputs.
 struct ProjGroup {
-    CUtensorMap tmx;
+    CUtensorMap tmx;  // the model's X rows (FP32, 32 x 128 boxes, 128-byte swizzle)
     const uint8_t *wt0, *wt1;
     const float *mcs_g, *col_scale;
     float *O, *norms, *vmax;
     int *err;
-    int64_t n, nstride;
-    int dk, npass, np, nkb;
+    int64_t n, nstride, ldo;
+    int dk, npass, np, nkb, il;
     float x_scale, norm_limit;
     SegCols segc;
 };
-// Rows of up to kMaxGroups models of one precision in one launch (a batch of
-// several collections): CTA b belongs to the group g with block_start[g] <=
-// b < block_start[g + 1].
+// The tiles of up to kMaxGroups models of one precision (one model for a
+// plain encode, a batch of several collections when serving): tile b belongs
+// to group g with tile_start[g] <= b < tile_start[g + 1], and within it to
+// row tile (b - tile_start[g]) / npass, column pass (b - tile_start[g]) % npass.
 struct ProjBatch {
     int ngroups;
     uint64_t wait_ns;
-    int64_t block_start[kMaxGroups + 1];
+    int64_t tile_start[kMaxGroups + 1];
     ProjGroup g[kMaxGroups];
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_proj_tc_grouped(const __grid_constant__ ProjBatch batch) {
-    const int64_t b = blockIdx.x;
+struct TileRef {
+    const ProjGroup *P;
+    int64_t row0;
+    int pass;
+};
+__device__ __forceinline__ TileRef decode_tile(const ProjBatch &batch, int64_t b) {
     int gi = 0;
-    while (gi + 1 < batch.ngroups && b >= batch.block_start[gi + 1]) ++gi;
+    while (gi + 1 < batch.ngroups && b >= batch.tile_start[gi + 1]) ++gi;
     const ProjGroup &P = batch.g[gi];
-    const int64_t lb = b - batch.block_start[gi];
-    proj_tile<MODE>(&P.tmx, lb / P.npass, (int)(lb % P.npass), P.wt0, P.wt1, P.n, P.dk, P.npass,
-                    P.np, P.nkb, P.mcs_g, P.x_scale, P.col_scale, P.O, P.dk, 1, P.norms, P.nstride,
-                    P.vmax, P.segc, P.err, batch.wait_ns, P.norm_limit);
+    const int64_t lb = b - batch.tile_start[gi];
+    return TileRef{&P, lb / P.npass * kBM, (int)(lb % P.npass)};
+}
+
+// bar.red.or over `threads` threads of named barrier `id`: true in every
+// participating thread if v is true in any (a decision all of them take
+// alike, so that none waits at a later barrier for one that has left).
+__device__ __forceinline__ bool named_any(int id, int threads, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+// Named barriers of the converter warps (ids; 0 is __syncthreads).
+constexpr int kBarNorm = 1, kBarStop = 2, kBarMcs = 3;
+
+// A persistent CTA: it takes tiles until the batch is done, from the device
+// work counter `queue` (one atomicAdd per tile) or, without one, tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Tile t of the CTA goes through a
+// ring of two slots in shared memory: the producer fetches it and publishes
+// it (tile_full), the MMA warp and the converter warps read it and release
+// the slot (tile_empty).  Every role keeps one running K-block counter `it`
+// over all of its tiles, so that the stage barriers' phases run on from
+// tile to tile: the producer loads the next tile's first stages while the
+// converter warps still drain the accumulator of the previous one, and the
+// MMA warp starts the next tile's MMAs once every converter warp has read
+// the accumulator (acc_empty).
+template <int MODE>
+__device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *queue) {
+    using C = Cfg<MODE>;
+    constexpr uint32_t SB = stage_bytes<MODE>();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + C::STAGES * SB);
+    uint64_t *conv = full + C::STAGES;
+    uint64_t *empty = conv + C::STAGES;
+    uint64_t *accf = empty + C::STAGES;
+    uint64_t *tile_full = accf + 1;       // 2
+    uint64_t *tile_empty = tile_full + 2;  // 2
+    uint64_t *acc_empty = tile_empty + 2;
+    int64_t *ring = (int64_t *)(acc_empty + 1);  // 2
+    uint32_t *tmem_slot = (uint32_t *)(ring + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *nrm_half = (float *)(smem + C::STAGES * SB + kBarArea);   // 128 floats
+    float *mcs = (float *)(smem + C::STAGES * SB + kBarArea + 512);  // nkb * BK floats
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t total = batch.tile_start[batch.ngroups];
+    const uint64_t wait_ns = batch.wait_ns;
+    // the error word of the first group takes the bounded waits' codes
+    int *err = batch.g[0].err;
+
+    {
+        const ProjGroup &P0 = batch.g[0];
+        for (int k = threadIdx.x; k < P0.nkb * C::BK; k += kThreads) mcs[k] = P0.mcs_g[k];
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], kConvWarps / 2);  // one group of converters per block
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tile_full[i], 1);
+            mbar_init(&tile_empty[i], 1 + kConvWarps);  // the MMA lane and every converter warp
+        }
+        mbar_init(acc_empty, kConvWarps);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(C::TMEM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;  // K blocks issued over all tiles
+            for (int t = 0;; ++t) {
+                const int slot = t & 1;
+                // the slot's tile t - 2 has been read by every consumer
+                if (t >= 2 &&
+                    !mbar_wait(&tile_empty[slot], (uint32_t)((t - 2) >> 1) & 1u, abort_flag, err, 1,
+                               wait_ns))
+                    break;
+                int64_t b = queue ? (int64_t)atomicAdd(queue, 1)
+                                  : (int64_t)blockIdx.x + (int64_t)t * gridDim.x;
+                if (b >= total) b = -1;
+                ring[slot] = b;
+                mbar_arrive(&tile_full[slot]);
+                if (b < 0) break;
+                const TileRef tr = decode_tile(batch, b);
+                const ProjGroup &P = *tr.P;
+                const CUtensorMap *tmxp = &P.tmx;
+                asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmxp) : "memory");
+                const uint32_t tx =
+                    (uint32_t)C::XBOX * kXBox + (uint32_t)C::NB * (uint32_t)P.np * 64u;
+                const int nkb = P.nkb;
+                const int row0 = (int)tr.row0;
+                // X boxes kPrefetch K blocks ahead are pulled into L2, so that
+                // the stage loads wait on L2 rather than on HBM
+                for (int kb = C::STAGES; kb < kPrefetch && kb < nkb; ++kb)
+#pragma unroll
+                    for (int bx = 0; bx < C::XBOX; ++bx)
+                        tma_prefetch_2d(tmxp, kb * C::BK + bx * 32, row0);
+                bool ok = true;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % (uint32_t)C::STAGES);
+                    const uint32_t ph = (it / (uint32_t)C::STAGES) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 1, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = smem + s * SB;
+                    mbar_expect_tx(&full[s], tx);
+#pragma unroll
+                    for (int bx = 0; bx < C::XBOX; ++bx)
+                        tma_load_2d(st + bx * kXBox, tmxp, kb * C::BK + bx * 32, row0, &full[s]);
+                    uint8_t *bs = st + b_offset<MODE>();
+                    const int64_t wo = ((int64_t)tr.pass * nkb + kb) * P.np * 64;
+                    bulk_load(bs, P.wt0 + wo, (uint32_t)P.np * 64u, &full[s]);
+                    if (C::NB == 2) bulk_load(bs + kBTile, P.wt1 + wo, (uint32_t)P.np * 64u, &full[s]);
+                    if (kb + kPrefetch < nkb)
+#pragma unroll
+                        for (int bx = 0; bx < C::XBOX; ++bx)
+                            tma_prefetch_2d(tmxp, (kb + kPrefetch) * C::BK + bx * 32, row0);
+                }
+                if (!ok) break;
+            }
+            // drain: the last loads of each stage must land before the CTA exits
+            for (uint32_t i = it > (uint32_t)C::STAGES ? it - (uint32_t)C::STAGES : 0u; i < it; ++i) {
+                const int s = (int)(i % (uint32_t)C::STAGES);
+                const uint32_t ph = (i / (uint32_t)C::STAGES) & 1u;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try(&full[s], ph) && globaltimer() - t0 < kWaitNs) {
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0;       // K blocks consumed over all tiles
+            uint32_t commits = 0;  // accumulator commits issued (one per tile)
+            bool ok = true;
+            for (int t = 0; ok; ++t) {
+                const int slot = t & 1;
+                if (!mbar_wait(&tile_full[slot], (uint32_t)(t >> 1) & 1u, abort_flag, err, 2, wait_ns))
+                    break;
+                const int64_t b = ring[slot];
+                mbar_arrive(&tile_empty[slot]);
+                if (b < 0) break;
+                const TileRef tr = decode_tile(batch, b);
+                const ProjGroup &P = *tr.P;
+                const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(P.np >> 3) << 17);
+                // the accumulator is free once every converter warp has read
+                // the previous tile's
+                if (t >= 1 && !mbar_wait(acc_empty, (uint32_t)(t - 1) & 1u, abort_flag, err, 2, wait_ns))
+                    break;
+                tc_fence_after();
+                for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+                    const int s = (int)(it % (uint32_t)C::STAGES);
+                    const uint32_t ph = (it / (uint32_t)C::STAGES) & 1u;
+                    if (!mbar_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + s * SB);
+                    const uint64_t b0 = umma_desc(st + b_offset<MODE>());
+                    const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
+                    // A of the stage in TMEM, 8 columns per 32-byte K step
+                    const uint32_t ahi = tmem + ta_col<MODE>(s, 0), alo = tmem + ta_col<MODE>(s, 1);
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
+                        const uint64_t off = (uint64_t)(kk * 2);
+                        const uint32_t ka = 8u * (uint32_t)kk;
+                        umma_ta<MODE>(tmem, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
+                        if (MODE == kSplit) {
+                            umma_ta<MODE>(tmem + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
+                            umma_ta<MODE>(tmem + kAcc2, alo + ka, b0 + off, idesc, 1u);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                }
+                // the tile's accumulator (after an abort: every MMA issued so far)
+                umma_commit(accf);
+                ++commits;
+            }
+            // at exit every MMA issued must be complete before TMEM is freed:
+            // the last accumulator commit's phase
+            if (commits > 0 && *abort_flag) {
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try(accf, (commits - 1u) & 1u) && globaltimer() - t0 < kWaitNs) {
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- converters: two groups of four warps, group h converting the K
+        // blocks kb = h, h + 2, ... of each tile (one thread per tile row, the
+        // whole block), so that two blocks are converted at once; then the
+        // tile's epilogue
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const int h = (warp - 2) >> 2;
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);  // the warp's TMEM lane quadrant
+        uint32_t base = 0;  // K blocks of this CTA's earlier tiles
+        // the first group's -c * s is in shared memory from the prologue
+        const ProjGroup *gcur = &batch.g[0];
+        bool ok = true;
+        for (int t = 0;; ++t) {
+            const int slot = t & 1;
+            int got = 0;
+            long long bl = -1;
+            if (lane == 0) {
+                got = mbar_wait(&tile_full[slot], (uint32_t)(t >> 1) & 1u, abort_flag, err, 3, wait_ns)
+                          ? 1
+                          : 0;
+                if (got) {
+                    bl = ring[slot];
+                    mbar_arrive(&tile_empty[slot]);
+                }
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            const int64_t b = (int64_t)__shfl_sync(0xffffffffu, bl, 0);
+            // the converter warps stop together (the end of the work, or a
+            // failed wait in any of them)
+            if (named_any(kBarStop, 32 * kConvWarps, !ok || !got || b < 0)) break;
+            const TileRef tr = decode_tile(batch, b);
+            const ProjGroup &P = *tr.P;
+            const int64_t row0 = tr.row0;
+            const int pass = tr.pass, nkb = P.nkb, np = P.np, dk = P.dk;
+            const float x_scale = P.x_scale;
+            const int col0 = pass * np;
+            if (tr.P != gcur) {
+                // the model's -c * s into shared memory (every converter warp
+                // is past its conversions of the earlier tiles)
+                for (int k = (int)threadIdx.x - 64; k < nkb * C::BK; k += 32 * kConvWarps)
+                    mcs[k] = P.mcs_g[k];
+                named_sync(kBarMcs, 32 * kConvWarps);
+                gcur = tr.P;
+            }
+            const bool row_ok = row0 + r < P.n;
+            float nrm = 0.f;
+            for (int kb = h; kb < nkb && ok; kb += 2) {
+                const uint32_t it = base + (uint32_t)kb;
+                const int s = (int)(it % (uint32_t)C::STAGES);
+                const uint32_t ph = (it / (uint32_t)C::STAGES) & 1u;
+                int gotk = 0;
+                // The other group may not have consumed this stage's previous
+                // block yet; a parity wait cannot tell phase p from phase p + 2,
+                // so first wait until the MMAs of block it - STAGES are done
+                // (the stage's barriers are then one phase behind this block at
+                // most).
+                if (lane == 0)
+                    gotk = (it < (uint32_t)C::STAGES ||
+                            mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 5, wait_ns)) &&
+                                   mbar_wait(&full[s], ph, abort_flag, err, 3, wait_ns)
+                               ? 1
+                               : 0;
+                gotk = __shfl_sync(0xffffffffu, gotk, 0);
+                if (!gotk) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *st = smem + s * SB;
+                const float *mk = mcs + kb * C::BK;
+                uint32_t wa[16];  // the row's A values of the stage (split: the hi part)
+                uint32_t wl[16];  // split: the lo part
+                convert_block<MODE>(st, mk, r, x_scale, nrm, wa, wl);
+                // TMEM column c of a buffer holds the row's values of K offsets
+                // c * (4 / element bytes) upward, lowest in the low bits
+                tmem_st16(tq + ta_col<MODE>(s, 0), wa);
+                if (MODE == kSplit) tmem_st16(tq + ta_col<MODE>(s, 1), wl);
+                tmem_st_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&conv[s]);
+            }
+            // |x - c|^2 of the row: the two groups' partial sums meet in shared memory
+            if (h == 1) nrm_half[r] = nrm;
+            named_sync(kBarNorm, 32 * kConvWarps);
+            if (h == 0 && pass == 0 && row_ok && ok) {
+                const float tot = nrm + nrm_half[r];
+                if (P.norms) P.norms[(row0 + r) * P.nstride] = tot / (x_scale * x_scale);
+                // |y|^2 >= max_k y_k^2: a row whose scaled, centred squared norm
+                // reaches norm_limit may hold a value the operand format cannot
+                // represent (the FP16 split overflows at 65504); a non-finite
+                // row fails the test too
+                if (!(tot < P.norm_limit)) atomicCAS(P.err, 0, kErrRange);
+            }
+            // ---- epilogue: accumulator row r, columns [h * np/2, (h+1) * np/2)
+            int ready = 0;
+            if (ok && lane == 0)
+                ready = mbar_wait(accf, (uint32_t)t & 1u, abort_flag, err, 4, wait_ns) ? 1 : 0;
+            ready = __shfl_sync(0xffffffffu, ready, 0);
+            if (!ready) ok = false;
+            if (ready) {
+                tc_fence_after();
+                tile_epilogue<MODE>(tq, h, lane, r, row0, row_ok, np, col0, dk, P.col_scale, P.O,
+                                    P.ldo, P.il, P.vmax, P.segc);
+            }
+            // the accumulator may take the next tile's MMAs once every
+            // converter warp has read it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+            base += (uint32_t)nkb;
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(C::TMEM)
+                     : "memory");
+    }
+}
+
+// Persistent projection of a serving batch: one CTA per SM, each taking tiles
+// of the batch until it is done (queue: the device work counter, zero at
+// launch; NULL: the static order blockIdx.x, blockIdx.x + gridDim.x, ...).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+k_proj_tc_persistent(const __grid_constant__ ProjBatch batch, int *queue) {
+    proj_persistent<MODE>(batch, queue);
 }
 
 // ------------------------------------------------------------- host side
@@ -935,51 +1303,81 @@ saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, floa
 }
 
 namespace {
-template <int MODE> saq_status launch_grouped_mode(const ProjJob *jobs, int njobs, cudaStream_t s) {
+// Operands and outputs of model m's rows X (n) as one group of a persistent
+// launch (interleaved output with v_max, |x - c|^2 into norms).
+template <int MODE>
+saq_status fill_group(ProjGroup *g, const ProjJob &j) {
+    const saq_model *m = j.m;
+    const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
+    saq_status st = make_map(&g->tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, j.X, (uint64_t)m->d,
+                             (uint64_t)j.n, 32, kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (st != SAQ_OK) return st;
+    g->wt0 = (const uint8_t *)m->tc.w_hi;
+    g->wt1 = (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi);
+    g->mcs_g = ex->mcs;
+    g->col_scale = m->tc.col_scale;
+    g->O = j.O;
+    g->norms = j.norms;
+    g->vmax = j.vmax;
+    g->err = j.err ? j.err : ex->err;
+    g->n = j.n;
+    g->nstride = j.nstride;
+    g->ldo = m->dk;
+    g->il = 1;
+    g->dk = m->dk;
+    g->npass = ex->npass;
+    g->np = ex->np;
+    g->nkb = m->tc.d_pad / Cfg<MODE>::BK;
+    g->x_scale = ex->x_scale;
+    g->norm_limit = MODE == kSplit ? 65504.f * 65504.f : INFINITY;
+    g->segc = seg_cols(m);
+    return SAQ_OK;
+}
+
+// SMs of the current device (one persistent CTA each).
+int sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev < 64 && cached[dev].load() > 0) return cached[dev].load();
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    if (dev < 64) cached[dev].store(sms);
+    return sms;
+}
+
+template <int MODE>
+saq_status launch_grouped_mode(const ProjJob *jobs, int njobs, int *queue, cudaStream_t s) {
     ProjBatch b;
     memset(&b, 0, sizeof(b));
     b.wait_ns = g_wait_ns.load();
-    b.block_start[0] = 0;
+    b.tile_start[0] = 0;
     int dpad_max = 0;
     for (int i = 0; i < njobs; ++i) {
         const ProjJob &j = jobs[i];
         const saq_model *m = j.m;
         if (j.n <= 0 || m->dk == 0) continue;
         const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
-        ProjGroup &g = b.g[b.ngroups];
-        saq_status st = make_map(&g.tmx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, j.X, (uint64_t)m->d,
-                                 (uint64_t)j.n, 32, kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+        saq_status st = fill_group<MODE>(&b.g[b.ngroups], j);
         if (st != SAQ_OK) return st;
-        g.wt0 = (const uint8_t *)m->tc.w_hi;
-        g.wt1 = (const uint8_t *)(m->tc.w_lo ? m->tc.w_lo : m->tc.w_hi);
-        g.mcs_g = ex->mcs;
-        g.col_scale = m->tc.col_scale;
-        g.O = j.O;
-        g.norms = j.norms;
-        g.vmax = j.vmax;
-        g.err = j.err ? j.err : ex->err;
-        g.n = j.n;
-        g.nstride = j.nstride;
-        g.dk = m->dk;
-        g.npass = ex->npass;
-        g.np = ex->np;
-        g.nkb = m->tc.d_pad / Cfg<MODE>::BK;
-        g.x_scale = ex->x_scale;
-        g.norm_limit = MODE == kSplit ? 65504.f * 65504.f : INFINITY;
-        g.segc = seg_cols(m);
         dpad_max = std::max(dpad_max, m->tc.d_pad);
-        b.block_start[b.ngroups + 1] = b.block_start[b.ngroups] + (j.n + kBM - 1) / kBM * ex->npass;
+        b.tile_start[b.ngroups + 1] = b.tile_start[b.ngroups] + (j.n + kBM - 1) / kBM * ex->npass;
         ++b.ngroups;
     }
     if (b.ngroups == 0) return SAQ_OK;
-    const int64_t blocks = b.block_start[b.ngroups];
-    if (blocks > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
+    const int64_t tiles = b.tile_start[b.ngroups];
+    if (tiles > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
     const uint32_t sm = smem_bytes<MODE>(dpad_max);
-    SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_grouped<MODE>,
+    SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_persistent<MODE>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // one CTA per SM (at most one per tile), the tiles taken in order from
+    // the work counter: the column passes of a row tile, consecutive tiles,
+    // run at about the same time and share X in L2
+    const int64_t grid = std::min<int64_t>(tiles, sm_count());
     {
         LaunchTimer lt_(kKindProject, s);
-        k_proj_tc_grouped<MODE><<<(unsigned)blocks, kThreads, sm, s>>>(b);
+        k_proj_tc_persistent<MODE><<<(unsigned)grid, kThreads, sm, s>>>(b, queue);
     }
     note_launches();
     SAQ_CUDA_CHECK(cudaGetLastError());
@@ -987,7 +1385,7 @@ template <int MODE> saq_status launch_grouped_mode(const ProjJob *jobs, int njob
 }
 }  // namespace
 
-saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, cudaStream_t s) {
+saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, int *queue, cudaStream_t s) {
     if (njobs < 1 || njobs > kMaxGroups)
         return set_error(SAQ_ERR_INVALID, "1..%d models per grouped launch", kMaxGroups);
     int prec = -1;
@@ -1004,9 +1402,9 @@ saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, cudaStream_
     }
     switch (prec) {
         case -1: return SAQ_OK;
-        case SAQ_PREC_FP32: return launch_grouped_mode<kSplit>(jobs, njobs, s);
-        case SAQ_PREC_BF16: return launch_grouped_mode<kBF16>(jobs, njobs, s);
-        case SAQ_PREC_FP8: return launch_grouped_mode<kFP8>(jobs, njobs, s);
+        case SAQ_PREC_FP32: return launch_grouped_mode<kSplit>(jobs, njobs, queue, s);
+        case SAQ_PREC_BF16: return launch_grouped_mode<kBF16>(jobs, njobs, queue, s);
+        case SAQ_PREC_FP8: return launch_grouped_mode<kFP8>(jobs, njobs, queue, s);
     }
     return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
 }

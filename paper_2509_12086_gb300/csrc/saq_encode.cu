@@ -111,7 +111,7 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
 
 // Rows of up to kMaxGroups models in one projection launch and one quantize
 // launch (a serving batch of several collections); see saq_internal.h.
-saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err) {
+saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err, int *queue) {
     if (njobs < 1 || njobs > kMaxGroups)
         return set_error(SAQ_ERR_INVALID, "1..%d models per grouped encode", kMaxGroups);
     ProjJob pj[kMaxGroups];
@@ -134,9 +134,10 @@ saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int 
         ++np;
     }
     if (np == 0) return SAQ_OK;
-    saq_status st = launch_project_tc_grouped(pj, np, s);
+    SAQ_CUDA_CHECK(cudaMemsetAsync(queue, 0, 2 * sizeof(int), s));
+    saq_status st = launch_project_tc_grouped(pj, np, queue, s);
     if (st != SAQ_OK) return st;
-    return launch_caq1_grouped(cj, np, s);
+    return launch_caq1_grouped(cj, np, queue + 1, s);
 }
 
 }  // namespace saq

@@ -56,7 +56,9 @@ struct Group {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    int *err_dev = nullptr;   // the batch's device error word (bounded waits, input range)
+    // the batch's device error word (bounded waits, input range), then the
+    // two work counters of its persistent launches
+    int *err_dev = nullptr;
     int *err_host = nullptr;  // its copy, written on the slot stream before the callback
     uint8_t *buf = nullptr;   // the batch's device memory (library pool)
     size_t bytes = 0;         // ... as reserved against the budget
@@ -310,7 +312,8 @@ bool launch_batch(saq_ingest *s, Slot &sl) {
             else st = saq::encode_rows(mg, jobs[0].X, jobs[0].n, jobs[0].codes, jobs[0].factors,
                                        jobs[0].scratch, jobs[0].n, sl.stream, sl.err_dev);
         } else {
-            st = saq::encode_grouped(jobs, (int)sl.groups.size(), sl.stream, sl.err_dev);
+            st = saq::encode_grouped(jobs, (int)sl.groups.size(), sl.stream, sl.err_dev,
+                                     sl.err_dev + 1);
         }
     }
     if (st == SAQ_OK && (cudaMemcpyAsync(sl.err_host, sl.err_dev, sizeof(int),
@@ -436,8 +439,8 @@ saq_status saq_ingest_open(saq_model *const *models, int32_t n_models,
     s->slots.resize((size_t)p->slots);
     for (Slot &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMalloc(&sl.err_dev, sizeof(int)) != cudaSuccess ||
-            cudaMemset(sl.err_dev, 0, sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&sl.err_dev, 4 * sizeof(int)) != cudaSuccess ||
+            cudaMemset(sl.err_dev, 0, 4 * sizeof(int)) != cudaSuccess ||
             cudaHostAlloc(&sl.err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
             free_slots(s);
             delete s;

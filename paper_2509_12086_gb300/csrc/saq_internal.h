@@ -147,8 +147,10 @@ struct ProjJob {
     float *vmax;
     int *err;  // NULL: the model's own error word
 };
-// Up to kMaxGroups models of one tensor-core precision in one launch.
-saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, cudaStream_t s);
+// Up to kMaxGroups models of one tensor-core precision in one persistent
+// launch whose CTAs take the tiles from the device work counter *queue
+// (zero at launch).
+saq_status launch_project_tc_grouped(const ProjJob *jobs, int njobs, int *queue, cudaStream_t s);
 bool tc_supported(const saq_model *m);
 void tc_release(saq_model *m);
 // Reads and clears the model's device error word of the tensor-core
@@ -180,7 +182,10 @@ struct CaqJob {
     uint8_t *codes;
     float *factors;
 };
-saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, cudaStream_t s);
+// Up to kMaxGroups models in one persistent launch whose warps take their
+// (model, segment, 32-row group) items from the device work counter *queue
+// (zero at launch).
+saq_status launch_caq1_grouped(const CaqJob *jobs, int njobs, int *queue, cudaStream_t s);
 // vmax of every (row, kept segment) from interleaved rows Oi (k_caq1.cu).
 // Lane-steps per second of the adjustment step on register-resident data
 // (saq_quantize_step_ceiling).
@@ -218,11 +223,12 @@ struct EncodeJob {
     float *factors;
     void *scratch;
 };
-// The encode of up to kMaxGroups models' rows with one projection launch
-// and one quantize launch; every model with kept dimensions must use the
-// tensor-core projection, all in one precision.  err as for
-// launch_project_tc.
-saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err);
+// The encode of up to kMaxGroups models' rows with one persistent projection
+// launch and one persistent quantize launch; every model with kept
+// dimensions must use the tensor-core projection, all in one precision.  err
+// as for launch_project_tc; queue: two device ints, the launches' work
+// counters (zeroed here on s before the launches).
+saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err, int *queue);
 // Estimator.
 saq_status launch_estimate_staged(const saq_model *m, const uint8_t *codes, const float *factors,
                                   int64_t n, const float *Q, const float *Qrot, const float *qn2,
