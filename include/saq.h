@@ -313,9 +313,11 @@ saq_status saq_set_wait_limit(uint64_t ns);
  * batches as slots free up: a batch takes the queued requests oldest first,
  * from up to 4 collections whose models use the same tensor-core precision,
  * at most max_batch_rows rows in all (large requests are split across
- * batches), and encodes them with ONE projection launch and ONE
- * quantize/adjust/pack launch over all its collections, on one of `slots`
- * streams, between one copy-in and one copy-out per request piece.  A model
+ * batches), and encodes them with ONE persistent projection launch and ONE
+ * persistent quantize/adjust/pack launch over all its collections (one CTA
+ * per SM, resp. as many blocks as stay resident, taking the batch's tiles and
+ * items from device work counters), on one of `slots` streams, between one
+ * copy-in and one copy-out per request piece.  A model
  * on the CUDA-core projection gets batches of its own.  Requests that arrive
  * while others are on the GPU join the next batch, so the copies and kernels
  * of different batches overlap.

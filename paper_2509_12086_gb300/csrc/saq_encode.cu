@@ -109,8 +109,9 @@ saq_status encode_rows(const saq_model *m, const float *X, int64_t n, uint8_t *c
     return SAQ_OK;
 }
 
-// Rows of up to kMaxGroups models in one projection launch and one quantize
-// launch (a serving batch of several collections); see saq_internal.h.
+// Rows of up to kMaxGroups models in one persistent projection launch and one
+// persistent quantize launch (a serving batch of several collections); see
+// saq_internal.h.
 saq_status encode_grouped(const EncodeJob *jobs, int njobs, cudaStream_t s, int *err, int *queue) {
     if (njobs < 1 || njobs > kMaxGroups)
         return set_error(SAQ_ERR_INVALID, "1..%d models per grouped encode", kMaxGroups);
