@@ -40,12 +40,12 @@ UNIT = "vectors/s"
 # a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "ee2a1a97648132496c5cf86ca543173524ad3b1c",
+    "projection": {"src": "k_tc.cu", "sha1": "f6e46857cbf166b9103a7173da003899ac10ccf8",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258274816 + 215818496) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "37cb46708aaed0a6dbb6dc70dce1a5cdcda8acb6",
+                   "bytes_per_row": (258195200 + 212701952) / 65536},
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "b17e324b42fd425587a7f23743add8af914609e2",
                              "workload": "c2_d960", "precision": "fp32",
-                             "bytes_per_row": (1558182400 + 35342336) / 65536},
+                             "bytes_per_row": (1558931712 + 35303680) / 65536},
 }
 
 
