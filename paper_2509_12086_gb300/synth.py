@@ -71,4 +71,5 @@ WORKLOADS = {
     "c2_d960": dict(n=1_000_000, d=960, alpha=0.8, avg_bits=4.0, rounds=6, nq=10_000),
     "c3_d1536": dict(n=1_000_000, d=1536, alpha=0.6, avg_bits=2.0, rounds=6, nq=1000),
     "c4_d3072": dict(n=500_000, d=3072, alpha=0.5, avg_bits=1.0, rounds=6, nq=1000),
+    "c4_d3072_8b": dict(n=500_000, d=3072, alpha=0.5, avg_bits=8.0, rounds=6, nq=1000),
 }
