@@ -70,7 +70,10 @@ constexpr int kNPMax = 256;         // output columns per tile at most (UMMA N)
 // the split form's column passes: two accumulators of at most 192 columns
 // and four hi/lo A buffers of 32 columns share the 512 TMEM columns
 constexpr int kSplitNP = 192;
-constexpr int kPrefetch = 8;        // X boxes are prefetched into L2 this many K blocks ahead
+// X boxes are prefetched into L2 this many K blocks ahead (measured at d =
+// 960 / 1536 / 3072: 4 ahead beats 8 by 1% / 0.2% / 2-4% and 16 or 32 lose
+// 1-13%; without a prefetch the projection is 8-20% slower)
+constexpr int kPrefetch = 4;
 constexpr int kAcc2 = 256;          // TMEM column of the split mode's correction accumulator
 constexpr int kConvWarps = 8;
 // error word: 1..5 the role whose wait timed out; kErrRange an input row
