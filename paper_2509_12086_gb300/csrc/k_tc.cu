@@ -831,9 +831,14 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
                 const TileRef tr = decode_tile(batch, b);
                 const ProjGroup &P = *tr.P;
                 const CUtensorMap *tmxp = &P.tmx;
+                // the tile's fields in registers: a read through the batch
+                // reference would be repeated after every asm with a memory
+                // clobber in the loop
+                const uint8_t *wt0 = P.wt0, *wt1 = P.wt1;
+                const int np = P.np;
                 asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmxp) : "memory");
                 const uint32_t tx =
-                    (uint32_t)C::XBOX * kXBox + (uint32_t)C::NB * (uint32_t)P.np * 64u;
+                    (uint32_t)C::XBOX * kXBox + (uint32_t)C::NB * (uint32_t)np * 64u;
                 const int nkb = P.nkb;
                 const int row0 = (int)tr.row0;
                 // X boxes kPrefetch K blocks ahead are pulled into L2, so that
@@ -856,9 +861,9 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
                     for (int bx = 0; bx < C::XBOX; ++bx)
                         tma_load_2d(st + bx * kXBox, tmxp, kb * C::BK + bx * 32, row0, &full[s]);
                     uint8_t *bs = st + b_offset<MODE>();
-                    const int64_t wo = ((int64_t)tr.pass * nkb + kb) * P.np * 64;
-                    bulk_load(bs, P.wt0 + wo, (uint32_t)P.np * 64u, &full[s]);
-                    if (C::NB == 2) bulk_load(bs + kBTile, P.wt1 + wo, (uint32_t)P.np * 64u, &full[s]);
+                    const int64_t wo = ((int64_t)tr.pass * nkb + kb) * np * 64;
+                    bulk_load(bs, wt0 + wo, (uint32_t)np * 64u, &full[s]);
+                    if (C::NB == 2) bulk_load(bs + kBTile, wt1 + wo, (uint32_t)np * 64u, &full[s]);
                     if (kb + kPrefetch < nkb)
 #pragma unroll
                         for (int bx = 0; bx < C::XBOX; ++bx)
@@ -891,12 +896,13 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
                 const TileRef tr = decode_tile(batch, b);
                 const ProjGroup &P = *tr.P;
                 const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(P.np >> 3) << 17);
+                const int nkb = P.nkb;
                 // the accumulator is free once every converter warp has read
                 // the previous tile's
                 if (t >= 1 && !mbar_wait(acc_empty, (uint32_t)(t - 1) & 1u, abort_flag, err, 2, wait_ns))
                     break;
                 tc_fence_after();
-                for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % (uint32_t)C::STAGES);
                     const uint32_t ph = (it / (uint32_t)C::STAGES) & 1u;
                     if (!mbar_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) {
