@@ -40,9 +40,9 @@ UNIT = "vectors/s"
 # a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "f6e46857cbf166b9103a7173da003899ac10ccf8",
+    "projection": {"src": "k_tc.cu", "sha1": "c6f832d7f5e9c6ea768b522eeed897ba89d3773f",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258195200 + 212701952) / 65536},
+                   "bytes_per_row": (258204672 + 211889408) / 65536},
     "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "b17e324b42fd425587a7f23743add8af914609e2",
                              "workload": "c2_d960", "precision": "fp32",
                              "bytes_per_row": (1558931712 + 35303680) / 65536},
