@@ -43,7 +43,7 @@ NCU_TRAFFIC = {
     "projection": {"src": "k_tc.cu", "sha1": "c6f832d7f5e9c6ea768b522eeed897ba89d3773f",
                    "workload": "c2_d960", "precision": "fp32",
                    "bytes_per_row": (258204672 + 211889408) / 65536},
-    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "b17e324b42fd425587a7f23743add8af914609e2",
+    "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ca5627b928766d09ea89518c720662654251fdcb",
                              "workload": "c2_d960", "precision": "fp32",
                              "bytes_per_row": (1558931712 + 35303680) / 65536},
 }

@@ -6,8 +6,10 @@
 // over the coordinates of the segment: step j loads coordinate j of all 32
 // vectors (one coalesced 128-byte line of the projected rows, stored
 // interleaved by groups of 32 rows: O_i[(g * d_kept + col) * 32 + lane]) and
-// their current codes (a byte scratch with the same layout), decides the
-// lane's move against that lane's own state and applies it.  Each lane
+// reads their current codes from the warp's code store (packed 8 per batch in
+// shared memory, k_caq1_sm, or one byte per coordinate in a global scratch
+// with the rows' layout, k_caq1, when a block's codes do not fit), decides
+// the lane's move against that lane's own state and applies it.  Each lane
 // therefore executes the paper's sequential scan exactly, and an accepted
 // move costs a predicated update instead of a serialising pass.
 //
