@@ -80,7 +80,7 @@ constexpr int kConvWarps = 8;
 // outside the operand format's range (or not finite)
 constexpr int kErrRange = 16;
 constexpr int kThreads = 64 + 32 * kConvWarps;
-// The double-buffered persistent form (BF16): four more warps that only
+// The double-buffered persistent form (BF16, FP8): four more warps that only
 // drain accumulators, so that one tile's epilogue runs beside the next
 // tile's MMAs.
 constexpr int kEpiWarps = 4;
@@ -111,10 +111,11 @@ static_assert(kTA + 16u * Cfg<kBF16>::STAGES <= 512u && kTA + 16u * Cfg<kFP8>::S
 static_assert(Cfg<kSplit>::STAGES == 4 && kSplitNP <= 192 && kAcc2 == 256 &&
                   kAcc2 + kSplitNP <= 448,
               "split-form TMEM map: accumulators and A buffers overlap");
-// The double-buffered BF16 form: accumulators at columns 0 and kAccDb (column
-// passes of at most kAccDb), the six A buffers from kTADb.
+// The double-buffered BF16 / FP8 form: accumulators at columns 0 and kAccDb
+// (column passes of at most kAccDb), the A buffers (six or four) from kTADb.
 constexpr uint32_t kAccDb = 208, kTADb = 416;
-static_assert(2u * kAccDb <= kTADb && kTADb + 16u * Cfg<kBF16>::STAGES <= 512u,
+static_assert(2u * kAccDb <= kTADb && kTADb + 16u * Cfg<kBF16>::STAGES <= 512u &&
+                  kTADb + 16u * Cfg<kFP8>::STAGES <= 512u,
               "double-buffered TMEM map: accumulators and A buffers overlap");
 template <int MODE> __host__ __device__ constexpr uint32_t ta_col(int s, int part) {
     return MODE == kSplit ? (s < 2 ? 192u + 32u * (uint32_t)s : 448u + 32u * (uint32_t)(s - 2)) +
@@ -1193,7 +1194,7 @@ struct TcExtra {
     float x_scale = 1.f;
     int np = 0, npass = 0;
     int *err = nullptr;
-    bool db = false;  // BF16 on the double-buffered kernel (passes of at most kAccDb)
+    bool db = false;  // BF16 / FP8 on the double-buffered kernel (passes of at most kAccDb)
 };
 
 double pow2_near(double x) { return ldexp(1.0, (int)lround(log2(x))); }
@@ -1284,12 +1285,16 @@ saq_status model_build_tc(saq_model *m, int precision, cudaStream_t) {
     const int dpad = (m->d + BK - 1) / BK * BK;
     const int d = m->d, dk = m->dk;
     // balanced column passes of at most 256 columns (split: 192), multiples
-    // of 16.  BF16 runs on the double-buffered kernel, whose two accumulators
-    // hold at most kAccDb columns each, when that takes at most a quarter
-    // more passes (measured: d_kept = 960, five passes instead of four, 9%
-    // faster; 1536, eight instead of six, 11% slower than the per-tile kernel)
+    // of 16.  BF16 and FP8 run on the double-buffered kernel, whose two
+    // accumulators hold at most kAccDb columns each, when the tiles are short
+    // (d <= 1024: the hidden epilogue is a large share of a tile) and the
+    // narrower passes are at most a quarter more.  Measured against the
+    // per-tile kernel: d = 960, five passes instead of four, BF16 9% and FP8
+    // 15% faster; BF16 at d = 1536 (eight instead of six) 11% slower; FP8 at
+    // d = 3072 (ten instead of eight, 15 instead of 12) equal and 13% slower.
     const int p256 = (dk + kNPMax - 1) / kNPMax, pdb = (dk + (int)kAccDb - 1) / (int)kAccDb;
-    const bool db = precision == SAQ_PREC_BF16 && 4 * pdb <= 5 * p256;
+    const bool db = (precision == SAQ_PREC_BF16 || precision == SAQ_PREC_FP8) && d <= 1024 &&
+                    4 * pdb <= 5 * p256;
     const int npmax = precision == SAQ_PREC_FP32 ? kSplitNP : db ? (int)kAccDb : kNPMax;
     const int npass = (dk + npmax - 1) / npmax;
     const int np = ((dk + npass - 1) / npass + 15) / 16 * 16;
@@ -1382,9 +1387,10 @@ SegCols seg_cols(const saq_model *m) {
 }
 
 namespace {
-saq_status launch_bf16_single(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                              int il, float *norms, int64_t ns, float *vmax, int *err,
-                              cudaStream_t s);
+template <int MODE>
+saq_status launch_db_single(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
+                            int il, float *norms, int64_t ns, float *vmax, int *err,
+                            cudaStream_t s);
 }  // namespace
 
 saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, float *O,
@@ -1400,10 +1406,13 @@ saq_status launch_project_tc(const saq_model *m, const float *X, int64_t n, floa
             // the double-buffered persistent kernel where the model's passes
             // allow it, else a CTA per tile
             if (static_cast<const TcExtra *>(m->tc.extra)->db)
-                return launch_bf16_single(m, X, n, O, ldo, layout == kInterleaved ? 1 : 0, norms2,
-                                          norms_stride, vmax, err, s);
+                return launch_db_single<kBF16>(m, X, n, O, ldo, layout == kInterleaved ? 1 : 0,
+                                               norms2, norms_stride, vmax, err, s);
             return launch_mode<kBF16>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, err, s);
         case SAQ_PREC_FP8:
+            if (static_cast<const TcExtra *>(m->tc.extra)->db)
+                return launch_db_single<kFP8>(m, X, n, O, ldo, layout == kInterleaved ? 1 : 0,
+                                              norms2, norms_stride, vmax, err, s);
             return launch_mode<kFP8>(m, X, n, O, ldo, layout, norms2, norms_stride, vmax, err, s);
     }
     return set_error(SAQ_ERR_INVALID, "tensor-core operands not built");
@@ -1467,14 +1476,22 @@ saq_status launch_persistent(const ProjBatch &b, int dpad_max, int *queue, bool 
     if (tiles > 0x7FFFFFFF) return set_error(SAQ_ERR_UNSUPPORTED, "too many rows in one call");
     const uint32_t sm = smem_bytes<MODE>(dpad_max);
     const int64_t grid = std::min<int64_t>(tiles, sm_count());
-    if (MODE == kBF16 && db) {
-        SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_db<kBF16>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        LaunchTimer lt_(kKindProject, s);
-        k_proj_tc_db<kBF16><<<(unsigned)grid, kThreadsDb, sm, s>>>(b, queue);
-    } else {
-        SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_persistent<MODE>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if constexpr (MODE != kSplit) {
+        if (db) {
+            SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_db<MODE>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            {
+                LaunchTimer lt_(kKindProject, s);
+                k_proj_tc_db<MODE><<<(unsigned)grid, kThreadsDb, sm, s>>>(b, queue);
+            }
+            note_launches();
+            SAQ_CUDA_CHECK(cudaGetLastError());
+            return SAQ_OK;
+        }
+    }
+    SAQ_CUDA_CHECK(cudaFuncSetAttribute(k_proj_tc_persistent<MODE>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
         LaunchTimer lt_(kKindProject, s);
         k_proj_tc_persistent<MODE><<<(unsigned)grid, kThreads, sm, s>>>(b, queue);
     }
@@ -1509,18 +1526,19 @@ saq_status launch_grouped_mode(const ProjJob *jobs, int njobs, int *queue, cudaS
     return launch_persistent<MODE>(b, dpad_max, queue, db, s);
 }
 
-// One model's rows on the double-buffered BF16 kernel, with a work counter
-// of its own from the stream-ordered pool (freed after the launch on s).
-saq_status launch_bf16_single(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
-                              int il, float *norms, int64_t ns, float *vmax, int *err,
-                              cudaStream_t s) {
+// One model's rows on the double-buffered kernel, with a work counter of its
+// own from the stream-ordered pool (freed after the launch on s).
+template <int MODE>
+saq_status launch_db_single(const saq_model *m, const float *X, int64_t n, float *O, int64_t ldo,
+                            int il, float *norms, int64_t ns, float *vmax, int *err,
+                            cudaStream_t s) {
     const TcExtra *ex = static_cast<const TcExtra *>(m->tc.extra);
     ProjBatch b;
     memset(&b, 0, sizeof(b));
     b.ngroups = 1;
     b.wait_ns = g_wait_ns.load();
     saq_status st =
-        fill_group<kBF16>(&b.g[0], ProjJob{m, X, n, O, norms, ns, vmax, err}, ldo, il);
+        fill_group<MODE>(&b.g[0], ProjJob{m, X, n, O, norms, ns, vmax, err}, ldo, il);
     if (st != SAQ_OK) return st;
     b.tile_start[0] = 0;
     b.tile_start[1] = (n + kBM - 1) / kBM * ex->npass;
@@ -1530,7 +1548,7 @@ saq_status launch_bf16_single(const saq_model *m, const float *X, int64_t n, flo
     st = SAQ_OK;
     if (cudaMemsetAsync(queue, 0, sizeof(int), s) != cudaSuccess)
         st = set_error(SAQ_ERR_CUDA, "work counter reset failed");
-    if (st == SAQ_OK) st = launch_persistent<kBF16>(b, m->tc.d_pad, queue, true, s);
+    if (st == SAQ_OK) st = launch_persistent<MODE>(b, m->tc.d_pad, queue, true, s);
     cudaFreeAsync(queue, s);
     return st;
 }
