@@ -40,7 +40,7 @@ UNIT = "vectors/s"
 # a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "9aba8fcf741f8766245d90e08d9023de50cb46c8",
+    "projection": {"src": "k_tc.cu", "sha1": "4e54a5969d068c92237a61e2b17f9aae498e8b02",
                    "workload": "c2_d960", "precision": "fp32",
                    "bytes_per_row": (258470912 + 214775808) / 65536},
     "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ca5627b928766d09ea89518c720662654251fdcb",

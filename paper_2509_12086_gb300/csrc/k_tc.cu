@@ -759,14 +759,18 @@ constexpr int kBarNorm = 1, kBarStop = 2, kBarMcs = 3;
 // A persistent CTA: it takes tiles until the batch is done, from the device
 // work counter `queue` (one atomicAdd per tile) or, without one, tiles
 // blockIdx.x, blockIdx.x + gridDim.x, ...  Tile t of the CTA goes through a
-// ring of two slots in shared memory: the producer fetches it and publishes
-// it (tile_full), the MMA warp and the converter warps read it and release
-// the slot (tile_empty).  Every role keeps one running K-block counter `it`
-// over all of its tiles, so that the stage barriers' phases run on from
-// tile to tile: the producer loads the next tile's first stages while the
-// converter warps still drain the accumulator of the previous one, and the
-// MMA warp starts the next tile's MMAs once every converter warp has read
-// the accumulator (acc_empty).
+// ring of slots in shared memory (two; four with DB): the producer fetches it
+// and publishes it (tile_full), every other role reads it and releases the
+// slot (tile_empty).  Every role keeps one running K-block counter `it` over
+// all of its tiles, so that the stage barriers' phases run on from tile to
+// tile and the producer loads the next tile's first stages while the
+// previous tile is still being drained.
+// Without DB the converter warps also drain the one accumulator, and the
+// MMA warp starts the next tile's MMAs once every converter warp has read it
+// (acc_empty).  With DB (BF16 / FP8, passes of at most kAccDb columns) tile t
+// accumulates into accumulator t % 2 and four more warps drain it, so that
+// its epilogue runs beside tile t + 1's MMAs; the MMA warp waits only for the
+// epilogue of tile t - 1 (acc_empty[t % 2]).
 template <int MODE, bool DB>
 __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *queue) {
     using C = Cfg<MODE>;
