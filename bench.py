@@ -40,9 +40,9 @@ UNIT = "vectors/s"
 # a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "4e54a5969d068c92237a61e2b17f9aae498e8b02",
+    "projection": {"src": "k_tc.cu", "sha1": "63b6db1be9d1a8bf9f7c3dd6edf35d15f8a070e9",
                    "workload": "c2_d960", "precision": "fp32",
-                   "bytes_per_row": (258470912 + 214775808) / 65536},
+                   "bytes_per_row": (258271744 + 212475904) / 65536},
     "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ca5627b928766d09ea89518c720662654251fdcb",
                              "workload": "c2_d960", "precision": "fp32",
                              "bytes_per_row": (1558931712 + 35303680) / 65536},
