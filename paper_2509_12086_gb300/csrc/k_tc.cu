@@ -211,6 +211,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         }
     }
 }
+// mbar_wait by every lane of a converged warp; the result is the same in all
+// of them.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err, int code, uint64_t limit_ns) {
+    const bool r = mbar_wait(bar, parity, abort_flag, err, code, limit_ns);
+    return __all_sync(0xffffffffu, r);
+}
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             uint64_t *bar) {
     asm volatile(
@@ -290,6 +297,30 @@ __device__ __forceinline__ void tmem_st_wait() {
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+// The same two instructions executed by a whole warp: one lane, elected
+// inside the instruction sequence, issues it (the warp must be converged).
+template <int MODE>
+__device__ __forceinline__ void umma_ta_elect(uint32_t dtm, uint32_t atm, uint64_t b, uint32_t idesc,
+                                              uint32_t acc) {
+    if (MODE == kFP8) {
+        asm volatile(
+            "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+            "r"(atm), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+            "r"(atm), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void umma_commit_elect(uint64_t *bar) {
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
             smem_u32(bar))
         : "memory");
 }
@@ -905,64 +936,68 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
-            uint32_t it = 0;       // K blocks consumed over all tiles
-            uint32_t commits = 0;  // accumulator commits issued (one per tile)
-            bool ok = true;
-            for (int t = 0; ok; ++t) {
-                const int slot = t % R;
-                if (!mbar_wait(&tile_full[slot], (uint32_t)(t / R) & 1u, abort_flag, err, 2, wait_ns))
+        // The whole warp runs the MMA loop, so that its control flow and the
+        // operands of the tcgen05 instructions are warp-uniform; one lane,
+        // elected inside each instruction, issues the MMAs and commits.
+        uint32_t it = 0;       // K blocks consumed over all tiles
+        uint32_t commits = 0;  // accumulator commits issued (one per tile)
+        bool ok = true;
+        for (int t = 0; ok; ++t) {
+            const int slot = t % R;
+            if (!warp_wait(&tile_full[slot], (uint32_t)(t / R) & 1u, abort_flag, err, 2, wait_ns))
+                break;
+            const int64_t b = ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tile_empty[slot]);
+            if (b < 0) break;
+            const TileRef tr = decode_tile(batch, b);
+            const ProjGroup &P = *tr.P;
+            const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(P.np >> 3) << 17);
+            const int nkb = P.nkb;
+            // tile t's accumulator (DB: the two alternate) is free once its
+            // previous tile has been read
+            const int a = DB ? (t & 1) : 0;
+            const uint32_t dacc = tmem + (uint32_t)a * kAccDb;
+            if (DB ? (t >= 2 && !warp_wait(&acc_empty[a], (uint32_t)((t >> 1) - 1) & 1u, abort_flag,
+                                           err, 2, wait_ns))
+                   : (t >= 1 && !warp_wait(acc_empty, (uint32_t)(t - 1) & 1u, abort_flag, err, 2,
+                                           wait_ns)))
+                break;
+            tc_fence_after();
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = (int)(it % (uint32_t)C::STAGES);
+                const uint32_t ph = (it / (uint32_t)C::STAGES) & 1u;
+                if (!warp_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) {
+                    ok = false;
                     break;
-                const int64_t b = ring[slot];
-                mbar_arrive(&tile_empty[slot]);
-                if (b < 0) break;
-                const TileRef tr = decode_tile(batch, b);
-                const ProjGroup &P = *tr.P;
-                const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(P.np >> 3) << 17);
-                const int nkb = P.nkb;
-                // tile t's accumulator (DB: the two alternate) is free once its
-                // previous tile has been read
-                const int a = DB ? (t & 1) : 0;
-                const uint32_t dacc = tmem + (uint32_t)a * kAccDb;
-                if (DB ? (t >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((t >> 1) - 1) & 1u,
-                                               abort_flag, err, 2, wait_ns))
-                       : (t >= 1 && !mbar_wait(acc_empty, (uint32_t)(t - 1) & 1u, abort_flag, err, 2,
-                                               wait_ns)))
-                    break;
-                tc_fence_after();
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
-                    const int s = (int)(it % (uint32_t)C::STAGES);
-                    const uint32_t ph = (it / (uint32_t)C::STAGES) & 1u;
-                    if (!mbar_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t st = smem_u32(smem + s * SB);
-                    const uint64_t b0 = umma_desc(st + b_offset<MODE>());
-                    const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
-                    // A of the stage in TMEM, 8 columns per 32-byte K step
-                    const uint32_t ahi = tmem + (DB ? kTADb + 16u * (uint32_t)s : ta_col<MODE>(s, 0));
-                    const uint32_t alo = tmem + ta_col<MODE>(s, 1);
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
-                        const uint64_t off = (uint64_t)(kk * 2);
-                        const uint32_t ka = 8u * (uint32_t)kk;
-                        umma_ta<MODE>(dacc, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
-                        if (MODE == kSplit) {
-                            umma_ta<MODE>(tmem + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
-                            umma_ta<MODE>(tmem + kAcc2, alo + ka, b0 + off, idesc, 1u);
-                        }
-                    }
-                    umma_commit(&empty[s]);
                 }
-                // the tile's accumulator (after an abort: every MMA issued so far)
-                umma_commit(&accf[a]);
-                ++commits;
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * SB);
+                const uint64_t b0 = umma_desc(st + b_offset<MODE>());
+                const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
+                // A of the stage in TMEM, 8 columns per 32-byte K step
+                const uint32_t ahi = tmem + (DB ? kTADb + 16u * (uint32_t)s : ta_col<MODE>(s, 0));
+                const uint32_t alo = tmem + ta_col<MODE>(s, 1);
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
+                    const uint64_t off = (uint64_t)(kk * 2);
+                    const uint32_t ka = 8u * (uint32_t)kk;
+                    umma_ta_elect<MODE>(dacc, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
+                    if (MODE == kSplit) {
+                        umma_ta_elect<MODE>(tmem + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
+                        umma_ta_elect<MODE>(tmem + kAcc2, alo + ka, b0 + off, idesc, 1u);
+                    }
+                }
+                umma_commit_elect(&empty[s]);
             }
-            // at exit every MMA issued must be complete before TMEM is freed
-            if (commits > 0) {
-                umma_commit(mma_done);
+            // the tile's accumulator (after an abort: every MMA issued so far)
+            umma_commit_elect(&accf[a]);
+            ++commits;
+        }
+        // at exit every MMA issued must be complete before TMEM is freed
+        if (commits > 0) {
+            umma_commit_elect(mma_done);
+            if (lane == 0) {
                 const uint64_t t0 = globaltimer();
                 while (!mbar_try(mma_done, 0) && globaltimer() - t0 < kWaitNs) {
                 }
