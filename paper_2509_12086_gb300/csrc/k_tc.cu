@@ -10,8 +10,11 @@
 //               MMA reads (NP rows of 64 bytes, 64-byte swizzle), so each
 //               operand tile is one contiguous bulk copy instead of NP
 //               64-byte rows of a tensor copy;
-//   warp 1      TMEM owner and MMA issuer (one elected lane): tcgen05.mma,
-//               accumulator 128 lanes x NP FP32 columns in TMEM;
+//   warp 1      TMEM owner and MMA issuer: the whole warp runs the K loop
+//               and one lane, elected inside each instruction, issues the
+//               tcgen05.mma and commits (a loop run by one lane alone issued
+//               them about 4% slower at d = 960, FP32); accumulator 128
+//               lanes x NP FP32 columns in TMEM;
 //   warps 2-9   converters, then epilogue.  Two groups of four warps take
 //               alternate K blocks (two blocks in conversion at once); in a
 //               group one thread per tile row reads the staged X values,
@@ -265,23 +268,6 @@ template <int MODE> __host__ __device__ constexpr uint32_t umma_idesc_base() {
     d |= (uint32_t)(kBM >> 4) << 24;
     return d;
 }
-// tcgen05.mma with the A operand in TMEM (column address `atm`, 128 lanes),
-// B from shared memory (descriptor b), D in TMEM at dtm
-template <int MODE>
-__device__ __forceinline__ void umma_ta(uint32_t dtm, uint32_t atm, uint64_t b, uint32_t idesc,
-                                        uint32_t acc) {
-    if (MODE == kFP8) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
-            "r"(atm), "l"(b), "r"(idesc), "r"(acc));
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
-            "r"(atm), "l"(b), "r"(idesc), "r"(acc));
-    }
-}
 // 16 consecutive 32-bit TMEM columns of the warp's lane quadrant, one word per
 // column from each thread (its own lane), and the wait for them
 __device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&w)[16]) {
@@ -294,14 +280,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&w)[16]) 
 __device__ __forceinline__ void tmem_st_wait() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-// The same two instructions executed by a whole warp: one lane, elected
-// inside the instruction sequence, issues it (the warp must be converged).
+// tcgen05.mma with the A operand in TMEM (column address `atm`, 128 lanes),
+// B from shared memory (descriptor b), D in TMEM at dtm, and tcgen05.commit
+// of the MMAs issued so far to an mbarrier.  Both are executed by a whole,
+// converged warp, and one lane, elected inside the instruction sequence,
+// issues them: a loop run by the whole warp keeps its control flow and the
+// instructions' operands warp-uniform, which the MMA issue rate depends on.
 template <int MODE>
 __device__ __forceinline__ void umma_ta_elect(uint32_t dtm, uint32_t atm, uint64_t b, uint32_t idesc,
                                               uint32_t acc) {
@@ -614,32 +598,34 @@ __device__ __forceinline__ void proj_tile(
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(np >> 3) << 17);
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % C::STAGES;
-                const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
-                if (!mbar_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) break;
-                tc_fence_after();
-                const uint32_t st = smem_u32(smem + s * SB);
-                const uint64_t b0 = umma_desc(st + b_offset<MODE>());
-                const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
-                // A of the stage in TMEM, 8 columns per 32-byte K step
-                const uint32_t ahi = tmem + ta_col<MODE>(s, 0), alo = tmem + ta_col<MODE>(s, 1);
+        // The whole warp runs the K loop (warp-uniform control flow and
+        // operands, the TMEM base through a warp reduction); one lane, elected
+        // inside each instruction, issues the MMAs and commits.
+        const uint32_t tmw = __reduce_or_sync(0xffffffffu, tmem);
+        const uint32_t idesc = umma_idesc_base<MODE>() | ((uint32_t)(np >> 3) << 17);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % C::STAGES;
+            const uint32_t ph = (uint32_t)(kb / C::STAGES) & 1u;
+            if (!warp_wait(&conv[s], ph, abort_flag, err, 2, wait_ns)) break;
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * SB);
+            const uint64_t b0 = umma_desc(st + b_offset<MODE>());
+            const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
+            // A of the stage in TMEM, 8 columns per 32-byte K step
+            const uint32_t ahi = tmw + ta_col<MODE>(s, 0), alo = tmw + ta_col<MODE>(s, 1);
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
-                    const uint64_t off = (uint64_t)(kk * 2);
-                    const uint32_t ka = 8u * (uint32_t)kk;
-                    umma_ta<MODE>(tmem, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
-                    if (MODE == kSplit) {
-                        umma_ta<MODE>(tmem + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
-                        umma_ta<MODE>(tmem + kAcc2, alo + ka, b0 + off, idesc, 1u);
-                    }
+            for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
+                const uint64_t off = (uint64_t)(kk * 2);
+                const uint32_t ka = 8u * (uint32_t)kk;
+                umma_ta_elect<MODE>(tmw, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
+                if (MODE == kSplit) {
+                    umma_ta_elect<MODE>(tmw + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
+                    umma_ta_elect<MODE>(tmw + kAcc2, alo + ka, b0 + off, idesc, 1u);
                 }
-                umma_commit(&empty[s]);
             }
-            umma_commit(accf);
+            umma_commit_elect(&empty[s]);
         }
+        umma_commit_elect(accf);
         __syncwarp();
     } else {
         // ---- converters: two groups of four warps, group h converting the K
@@ -939,6 +925,9 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
         // The whole warp runs the MMA loop, so that its control flow and the
         // operands of the tcgen05 instructions are warp-uniform; one lane,
         // elected inside each instruction, issues the MMAs and commits.
+        // the TMEM base and each tile number through a warp reduction: values
+        // the compiler then treats as warp-uniform
+        const uint32_t tmw = __reduce_or_sync(0xffffffffu, tmem);
         uint32_t it = 0;       // K blocks consumed over all tiles
         uint32_t commits = 0;  // accumulator commits issued (one per tile)
         bool ok = true;
@@ -946,8 +935,7 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
             const int slot = t % R;
             if (!warp_wait(&tile_full[slot], (uint32_t)(t / R) & 1u, abort_flag, err, 2, wait_ns))
                 break;
-            const int64_t b = ring[slot];
-            __syncwarp();
+            const int64_t b = (int64_t)__reduce_max_sync(0xffffffffu, (int)ring[slot]);
             if (lane == 0) mbar_arrive(&tile_empty[slot]);
             if (b < 0) break;
             const TileRef tr = decode_tile(batch, b);
@@ -957,7 +945,7 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
             // tile t's accumulator (DB: the two alternate) is free once its
             // previous tile has been read
             const int a = DB ? (t & 1) : 0;
-            const uint32_t dacc = tmem + (uint32_t)a * kAccDb;
+            const uint32_t dacc = tmw + (uint32_t)a * kAccDb;
             if (DB ? (t >= 2 && !warp_wait(&acc_empty[a], (uint32_t)((t >> 1) - 1) & 1u, abort_flag,
                                            err, 2, wait_ns))
                    : (t >= 1 && !warp_wait(acc_empty, (uint32_t)(t - 1) & 1u, abort_flag, err, 2,
@@ -976,16 +964,16 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
                 const uint64_t b0 = umma_desc(st + b_offset<MODE>());
                 const uint64_t b1 = umma_desc(st + b_offset<MODE>() + kBTile);
                 // A of the stage in TMEM, 8 columns per 32-byte K step
-                const uint32_t ahi = tmem + (DB ? kTADb + 16u * (uint32_t)s : ta_col<MODE>(s, 0));
-                const uint32_t alo = tmem + ta_col<MODE>(s, 1);
+                const uint32_t ahi = tmw + (DB ? kTADb + 16u * (uint32_t)s : ta_col<MODE>(s, 0));
+                const uint32_t alo = tmw + ta_col<MODE>(s, 1);
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {  // two 32-byte K steps per 64-byte row
                     const uint64_t off = (uint64_t)(kk * 2);
                     const uint32_t ka = 8u * (uint32_t)kk;
                     umma_ta_elect<MODE>(dacc, ahi + ka, b0 + off, idesc, (kb | kk) != 0);
                     if (MODE == kSplit) {
-                        umma_ta_elect<MODE>(tmem + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
-                        umma_ta_elect<MODE>(tmem + kAcc2, alo + ka, b0 + off, idesc, 1u);
+                        umma_ta_elect<MODE>(tmw + kAcc2, ahi + ka, b1 + off, idesc, (kb | kk) != 0);
+                        umma_ta_elect<MODE>(tmw + kAcc2, alo + ka, b0 + off, idesc, 1u);
                     }
                 }
                 umma_commit_elect(&empty[s]);
