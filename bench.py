@@ -40,7 +40,7 @@ UNIT = "vectors/s"
 # a launch's traffic is proportional to its rows.  A figure is reported only while the
 # kernel's source file is the one that was captured (SHA-1 below).
 NCU_TRAFFIC = {
-    "projection": {"src": "k_tc.cu", "sha1": "3bd2e8e61b8195ccf691f89fd8952e1255e59b6e",
+    "projection": {"src": "k_tc.cu", "sha1": "957519d74ad2b945597249c6b3734e933f4f3071",
                    "workload": "c2_d960", "precision": "fp32",
                    "bytes_per_row": (258402304 + 211736064) / 65536},
     "quantize_adjust_pack": {"src": "k_caq1.cu", "sha1": "ca5627b928766d09ea89518c720662654251fdcb",

@@ -833,7 +833,7 @@ __device__ __forceinline__ void proj_persistent(const ProjBatch &batch, int *que
         }
         for (int i = 0; i < R; ++i) {
             mbar_init(&tile_full[i], 1);
-            // the MMA lane, every converter warp and every epilogue warp
+            // the MMA warp, every converter warp and every epilogue warp
             mbar_init(&tile_empty[i], 1 + kConvWarps + (DB ? kEpiWarps : 0));
         }
         mbar_init(mma_done, 1);
